@@ -1,0 +1,215 @@
+/*
+ * paco.h -- C ABI of the PACO FFT library for one GB300 (sm_103a).
+ *
+ * PACO ("A Fully Cache-Oblivious Parallel FFT with One Global
+ * Redistribution") computes the canonical length-N DFT
+ *
+ *     y = Omega_N x,  (Omega_N)_{k,j} = w_N^{-kj},  w_N = exp(2*pi*i/N)
+ *
+ * (Sect. 2, "Model and Main Result") for N = N1*N2, N1 = b^m1, N2 = b^m2,
+ * as LocalFFT -> one fused base-b digit-reversal permutation -> LocalFFT
+ * (Sect. 3, Eq. (10)).  On one GPU the paper's p processors are p virtual
+ * slabs; its one global redistribution (PARA-CO-DRP_b, Sect. 4.2) is the HBM
+ * pass between the two stage kernels.
+ *
+ * Data layout (all entry points):
+ *   - Complex data are interleaved (re, im): PACO_C64 = two floats (8 B),
+ *     PACO_C128 = two doubles (16 B).  Buffers are device pointers unless an
+ *     entry point says "host", aligned to 16 bytes, holding `batch`
+ *     transforms back to back (stride N elements).
+ *   - Input of one transform: x in natural order, i.e. the row-major
+ *     N1 x N2 view X[j1, j2] = x[j1*N2 + j2] (Sect. 2, input view).
+ *   - Output of one transform: the row-major N2 x N1 view
+ *     Y[k2, k1] = y[k1 + k2*N1] (Eq. factor-swapped-output-view), which is
+ *     natural-order y when read flat.  Slab q' of the output (Eq. (3),
+ *     owner1 = floor(k1*p/N1)) is the column range k1 in [q'N1/p,(q'+1)N1/p).
+ *   - dir = -1 computes the paper's transform (w^{-kj}); dir = +1 computes the
+ *     unnormalised conjugate transform (w^{+kj}).  The paper defines only
+ *     the forward transform; +1 is this library's reading (the adjoint).
+ *
+ * Ownership: the caller owns every buffer passed in.  A plan owns its
+ * twiddle tables and a device status word; it holds no N-sized scratch.
+ * Execution entry points enqueue work on `stream` and return without
+ * synchronising; they allocate nothing.
+ *
+ * Errors: every entry point returns a paco_status_t (plan constructors that
+ * return a pointer return NULL instead).  On failure a message for the
+ * calling thread is available from paco_last_error().  Errors detected while
+ * kernels run are reported by paco_plan_check().
+ */
+#ifndef PACO_H
+#define PACO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without including the CUDA headers; NULL = legacy stream. */
+typedef struct CUstream_st *paco_stream_t;
+
+typedef struct paco_plan paco_plan_t;
+
+typedef enum {
+    PACO_OK = 0,
+    PACO_ERR_INVALID_ARG = 1, /* sizes, radix, p, pointers, dir out of contract */
+    PACO_ERR_UNSUPPORTED = 2, /* legal for the paper, not built here */
+    PACO_ERR_ALIASING = 3,    /* in == out where the entry point forbids it */
+    PACO_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+    PACO_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+    PACO_ERR_NOMEM = 6,       /* plan allocation failed */
+    PACO_ERR_DEVICE = 7       /* a device-side check set the status word */
+} paco_status_t;
+
+typedef enum {
+    PACO_C64 = 0,           /* complex float in/out, FP32 arithmetic */
+    PACO_C128 = 1,          /* complex double in/out, FP64 arithmetic */
+    PACO_C64_TC_BF16X3 = 2, /* complex float in/out; radix-16 sub-DFTs as
+                               3-term-split BF16 tensor-core products */
+    PACO_C64_TC_FP16 = 3    /* complex float in/out; radix-16 sub-DFTs as FP16
+                               tensor-core products with per-block scaling */
+} paco_dtype_t;
+
+/* Plan options for paco_plan_create_ex.  Zero fields take defaults. */
+typedef struct {
+    int64_t N1, N2;      /* the two factors, N = N1*N2 (Sect. 2) */
+    int b;               /* digit-reversal radix: 2, 4, 8 or 16 (b = 2^t) */
+    int p;               /* virtual slabs; 0 = default b^floor(min(m1,m2)/2),
+                            raised to b if that is 1 */
+    int64_t batch;       /* transforms per execute, >= 0 */
+    paco_dtype_t dtype;
+    int tile_w;          /* columns per tile; 0 = default */
+    int cluster;         /* CTAs per cluster (1, 2, 4, 8); 0 = default */
+} paco_plan_opts_t;
+
+/* Read-only description of a plan (paco_plan_info). */
+typedef struct {
+    int64_t N1, N2, N, batch;
+    int b, p, m1, m2;
+    paco_dtype_t dtype;
+    int slab_width_ok;           /* N1/p and N2/p span >= 128 B (Eq. (5)) */
+    int64_t items_per_pair;      /* N/p^2 (Eq. fused-global-pairwise-volume) */
+    int64_t h;                   /* (N/p)(1 - 1/p) (Eq. fused-global-h-volume) */
+    int64_t mu;                  /* N(1 - 1/p) (Eq. fused-global-total-volume) */
+    int stage_tile_w[2];         /* tile width used by stage 1 / stage 2 */
+    int stage_cluster[2];        /* cluster size used by stage 1 / stage 2 */
+    int stage_threads[2];        /* threads per CTA */
+    int stage_smem[2];           /* dynamic shared memory per CTA, bytes */
+} paco_plan_info_t;
+
+/*
+ * paco_plan_create -- plan `batch` PACO transforms of size N = N1*N2 with
+ * digit-reversal radix b (Sect. 2: b = 2^t, N1 = b^m1, N2 = b^m2, p | N1,
+ * p | N2, Eq. exact-divisibility) in precision `dtype`, on the current CUDA
+ * device.  Builds the twiddle tables in FP64 on the device and waits for
+ * them.  Returns NULL on error (paco_last_error() says why): N1 or N2 not a
+ * power of b, b not in {2,4,8,16}, N > 2^32, batch < 0, or a dtype that is
+ * not built.  The default p is described at paco_plan_opts_t.
+ */
+paco_plan_t *paco_plan_create(int64_t N1, int64_t N2, int b, int64_t batch,
+                              paco_dtype_t dtype);
+
+/* paco_plan_create_ex -- as paco_plan_create with explicit options (p, tile,
+ * cluster).  p must be a power of b with p >= 2, p | N1 and p | N2
+ * (Eq. exact-divisibility).  Writes the plan to *out (NULL on error). */
+paco_status_t paco_plan_create_ex(paco_plan_t **out, const paco_plan_opts_t *opts);
+
+/* paco_plan_destroy -- free the plan's tables.  NULL is accepted.  The
+ * caller must ensure no work using the plan is still running. */
+void paco_plan_destroy(paco_plan_t *plan);
+
+/* paco_plan_info -- fill *info for the plan. */
+paco_status_t paco_plan_info(const paco_plan_t *plan, paco_plan_info_t *info);
+
+/*
+ * paco_execute -- y = PACO(x) for every transform of the batch (Theorem 3):
+ * Phase I (LocalFFT, output layout, Lemma 1) with the top-level twiddle and
+ * the full digit reversal pi_m of Eq. (full-middle-digit-reversal) fused into
+ * its stores (the PARA-CO-DRP_b middle stage, Sect. 4.2), then Phase III
+ * (LocalFFT, input layout) reading that layout.  `in` and `out` are device
+ * buffers of batch*N elements of the plan's dtype; `out` also holds the
+ * intermediate W = Z-hat (Eq. (17)) between the two kernels, so no scratch
+ * is used.  in == out, or overlapping buffers, return PACO_ERR_ALIASING.
+ * batch = 0 is a no-op.  Asynchronous on `stream`.
+ */
+paco_status_t paco_execute(paco_plan_t *plan, const void *in, void *out, int dir,
+                           paco_stream_t stream);
+
+/*
+ * paco_execute_stage1 -- Phase I and the fused middle stage only: writes
+ * W[u][v] = Z-hat[u, v] = Z[v, pi_m2(u)] with Z[v, c] = A[v, c] w_N^{dir*vc}
+ * and A the length-N1 column DFTs (Sect. 4.2, local pack and Eq. (17)),
+ * as a row-major N2 x N1 array per transform.  in != W required.
+ */
+paco_status_t paco_execute_stage1(paco_plan_t *plan, const void *in, void *W, int dir,
+                                  paco_stream_t stream);
+
+/*
+ * paco_execute_stage2 -- Phase III only: for every column v of W (N2 x N1,
+ * Eq. (17) layout), the length-N2 DFT of the logical input W[pi_m2(j)][v]
+ * (input-layout operator B_m2 = Omega P_pi, Lemma 1), written to
+ * out[k2][v].  W == out is allowed (in place); partial overlap is not.
+ */
+paco_status_t paco_execute_stage2(paco_plan_t *plan, const void *W, void *out, int dir,
+                                  paco_stream_t stream);
+
+/*
+ * paco_execute_phase1 -- Phase I alone, unfused: the output-layout local FFT
+ * A-tilde[a, c] = A[pi_m1(a), c] (Lemma 1, Eq. output-layout-local-operator)
+ * written as a row-major N1 x N2 array per transform, with no twiddle and no
+ * redistribution.  Together with paco_permute and paco_execute_stage2 it
+ * forms the unfused three-pass pipeline.  in != out required.
+ */
+paco_status_t paco_execute_phase1(paco_plan_t *plan, const void *in, void *out, int dir,
+                                  paco_stream_t stream);
+
+/*
+ * paco_permute -- the middle stage PARA-CO-DRP_b as a standalone pass
+ * (App. C.5): reads A-tilde (N1 x N2, layout of paco_execute_phase1) and
+ * writes W[pi_m2(c)][pi_m1(a)] = A-tilde[a][c] * w_N^{dir*pi_m1(a)*c}
+ * (N2 x N1), i.e. pack with the fused twiddle, the all-to-all of N/p^2-item
+ * blocks, the per-block transpose and the unpack, in one gather.  in != W.
+ */
+paco_status_t paco_permute(paco_plan_t *plan, const void *A_tilde, void *W, int dir,
+                           paco_stream_t stream);
+
+/*
+ * paco_execute_host -- paco_execute on HOST buffers: copies h_in (batch*N
+ * elements, pinned or pageable host memory) to the device buffer d_in,
+ * runs paco_execute(d_in -> d_out), and copies d_out back to h_out, all
+ * enqueued on `stream`; returns once the work is enqueued (synchronise the
+ * stream before reading h_out).  d_in and d_out are caller-owned device
+ * buffers of batch*N elements and must not overlap.
+ */
+paco_status_t paco_execute_host(paco_plan_t *plan, const void *h_in, void *h_out,
+                                void *d_in, void *d_out, int dir, paco_stream_t stream);
+
+/*
+ * paco_plan_check -- synchronise the device, then read and clear the plan's
+ * device status word.  Returns PACO_OK, PACO_ERR_DEVICE or PACO_ERR_TIMEOUT
+ * for errors raised by kernels since the last check, or PACO_ERR_CUDA.
+ */
+paco_status_t paco_plan_check(paco_plan_t *plan);
+
+/* paco_last_error -- message for the last failure on the calling thread
+ * ("" if none).  The string stays valid until the thread's next call. */
+const char *paco_last_error(void);
+
+/*
+ * paco_digit_reverse -- pi_ell(u) in base b (Sect. 3.2, App. A.1): the
+ * ell-digit base-b string of u written in reverse digit order; the same map
+ * the kernels compute.  Returns -1 if b is not in {2,4,8,16}, ell*log2(b)
+ * exceeds 31, or u >= b^ell.  Host-only, no GPU needed.
+ */
+int64_t paco_digit_reverse(int64_t u, int b, int ell);
+
+/* paco_version -- library version string. */
+const char *paco_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PACO_H */

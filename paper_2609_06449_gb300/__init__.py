@@ -1,0 +1,271 @@
+"""PACO FFT on one GB300 -- thin Python binding over the C ABI (include/paco.h).
+
+Every step of the transform runs in the CUDA kernels of ``libpaco.so``; this
+module only marshals arguments.  PyTorch supplies device memory and streams.
+There is no CPU fallback: importing the package raises if the library has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``).
+
+Entry points (same names as the C ABI):
+
+* ``Plan(N1, N2, b, batch, dtype, p=0, tile_w=0, cluster=0)`` --
+  ``paco_plan_create_ex``; ``.execute(in_ptr, out_ptr, dir, stream)`` etc.
+* ``fft(x, N1, N2, b, p=0, dir=-1)`` -- torch tensors on the GPU.
+* ``PacoFFT`` -- ``torch.autograd.Function`` whose backward is the conjugate
+  transform (``dir=+1``).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+__all__ = [
+    "PacoError",
+    "Plan",
+    "lib",
+    "library_path",
+    "fft",
+    "PacoFFT",
+    "digit_reverse",
+    "C64",
+    "C128",
+    "C64_TC_BF16X3",
+    "C64_TC_FP16",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libpaco.so")
+
+C64, C128, C64_TC_BF16X3, C64_TC_FP16 = 0, 1, 2, 3
+
+_STATUS = {
+    0: "PACO_OK",
+    1: "PACO_ERR_INVALID_ARG",
+    2: "PACO_ERR_UNSUPPORTED",
+    3: "PACO_ERR_ALIASING",
+    4: "PACO_ERR_CUDA",
+    5: "PACO_ERR_TIMEOUT",
+    6: "PACO_ERR_NOMEM",
+    7: "PACO_ERR_DEVICE",
+}
+
+
+class PacoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [
+        ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("b", ctypes.c_int),
+        ("p", ctypes.c_int), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
+        ("tile_w", ctypes.c_int), ("cluster", ctypes.c_int),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("N", ctypes.c_int64),
+        ("batch", ctypes.c_int64), ("b", ctypes.c_int), ("p", ctypes.c_int),
+        ("m1", ctypes.c_int), ("m2", ctypes.c_int), ("dtype", ctypes.c_int),
+        ("slab_width_ok", ctypes.c_int), ("items_per_pair", ctypes.c_int64),
+        ("h", ctypes.c_int64), ("mu", ctypes.c_int64),
+        ("stage_tile_w", ctypes.c_int * 2), ("stage_cluster", ctypes.c_int * 2),
+        ("stage_threads", ctypes.c_int * 2), ("stage_smem", ctypes.c_int * 2),
+    ]
+
+
+def _load():
+    if not os.path.exists(library_path):
+        raise ImportError(
+            f"{library_path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(library_path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+    L.paco_plan_create.argtypes = [i64, i64, i32, i64, i32]
+    L.paco_plan_create.restype = vp
+    L.paco_plan_create_ex.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(PlanOpts)]
+    L.paco_plan_create_ex.restype = i32
+    L.paco_plan_destroy.argtypes = [vp]
+    L.paco_plan_destroy.restype = None
+    L.paco_plan_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+    L.paco_plan_info.restype = i32
+    for name in ("paco_execute", "paco_execute_stage1", "paco_execute_stage2",
+                 "paco_execute_phase1", "paco_permute"):
+        f = getattr(L, name)
+        f.argtypes = [vp, vp, vp, i32, vp]
+        f.restype = i32
+    L.paco_execute_host.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+    L.paco_execute_host.restype = i32
+    L.paco_plan_check.argtypes = [vp]
+    L.paco_plan_check.restype = i32
+    L.paco_last_error.argtypes = []
+    L.paco_last_error.restype = ctypes.c_char_p
+    L.paco_digit_reverse.argtypes = [i64, i32, i32]
+    L.paco_digit_reverse.restype = i64
+    L.paco_version.argtypes = []
+    L.paco_version.restype = ctypes.c_char_p
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise PacoError(status, lib.paco_last_error().decode())
+
+
+def digit_reverse(u: int, b: int, ell: int) -> int:
+    """pi_ell(u) in base b, as computed by the library (host function)."""
+    r = lib.paco_digit_reverse(int(u), int(b), int(ell))
+    if r < 0:
+        raise PacoError(1, "digit_reverse: bad argument")
+    return int(r)
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A PACO plan (``paco_plan_create_ex``).  Buffers are torch tensors or
+    raw device pointers; ``stream`` is a torch stream, a raw handle, or None
+    for torch's current stream."""
+
+    def __init__(self, N1: int, N2: int, b: int, batch: int = 1, dtype: int = C64,
+                 p: int = 0, tile_w: int = 0, cluster: int = 0):
+        o = PlanOpts(int(N1), int(N2), int(b), int(p), int(batch), int(dtype),
+                     int(tile_w), int(cluster))
+        h = ctypes.c_void_p()
+        _check(lib.paco_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))
+        self._h = h
+        inf = PlanInfo()
+        _check(lib.paco_plan_info(self._h, ctypes.byref(inf)))
+        self.info = inf
+        self.N1, self.N2, self.N = inf.N1, inf.N2, inf.N
+        self.b, self.p, self.batch, self.dtype = inf.b, inf.p, inf.batch, inf.dtype
+        self.m1, self.m2 = inf.m1, inf.m2
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.paco_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def execute(self, x, out, dir: int = -1, stream=None) -> None:
+        _check(lib.paco_execute(self._h, _ptr(x), _ptr(out), int(dir), _stream(stream)))
+
+    def execute_stage1(self, x, W, dir: int = -1, stream=None) -> None:
+        _check(lib.paco_execute_stage1(self._h, _ptr(x), _ptr(W), int(dir), _stream(stream)))
+
+    def execute_stage2(self, W, out, dir: int = -1, stream=None) -> None:
+        _check(lib.paco_execute_stage2(self._h, _ptr(W), _ptr(out), int(dir), _stream(stream)))
+
+    def execute_phase1(self, x, out, dir: int = -1, stream=None) -> None:
+        _check(lib.paco_execute_phase1(self._h, _ptr(x), _ptr(out), int(dir), _stream(stream)))
+
+    def permute(self, a_tilde, W, dir: int = -1, stream=None) -> None:
+        _check(lib.paco_permute(self._h, _ptr(a_tilde), _ptr(W), int(dir), _stream(stream)))
+
+    def execute_host(self, h_in, h_out, d_in, d_out, dir: int = -1, stream=None) -> None:
+        _check(lib.paco_execute_host(self._h, _ptr(h_in), _ptr(h_out), _ptr(d_in),
+                                     _ptr(d_out), int(dir), _stream(stream)))
+
+    def check(self) -> None:
+        _check(lib.paco_plan_check(self._h))
+
+
+_PLANS: dict = {}
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise TypeError(f"PACO takes complex64 or complex128 tensors, got {t.dtype}")
+
+
+def get_plan(N1: int, N2: int, b: int, batch: int, dtype: int, p: int = 0,
+             device: int | None = None) -> Plan:
+    import torch
+    dev = torch.cuda.current_device() if device is None else device
+    key = (N1, N2, b, batch, dtype, p, dev)
+    pl = _PLANS.get(key)
+    if pl is None:
+        with torch.cuda.device(dev):
+            pl = Plan(N1, N2, b, batch, dtype, p)
+        _PLANS[key] = pl
+    return pl
+
+
+def fft(x, N1: int, N2: int, b: int, p: int = 0, dir: int = -1, out=None):
+    """PACO transform of the last dimension of ``x`` (length N1*N2) for every
+    leading index: dir=-1 the paper's forward DFT, dir=+1 the unnormalised
+    conjugate transform.  ``x`` must be a contiguous complex64/complex128 CUDA
+    tensor; returns a new tensor (or fills ``out``)."""
+    import torch
+    if not x.is_cuda:
+        raise ValueError("PACO runs on the GPU: x must be a CUDA tensor")
+    N = int(N1) * int(N2)
+    if x.shape[-1] != N:
+        raise ValueError(f"last dimension {x.shape[-1]} != N1*N2 = {N}")
+    x = x.contiguous()
+    batch = x.numel() // N
+    if out is None:
+        out = torch.empty_like(x)
+    pl = get_plan(int(N1), int(N2), int(b), batch, _dtype_code(x), int(p), x.device.index)
+    pl.execute(x, out, dir)
+    return out
+
+
+try:
+    import torch as _torch
+
+    class PacoFFT(_torch.autograd.Function):
+        """y = PACO(x) with the hand-written backward grad_x = F^H grad_y,
+        F^H being the unnormalised conjugate transform (F is symmetric, so
+        F^H = conj(F)); it runs the same kernels with dir = +1."""
+
+        @staticmethod
+        def forward(ctx, x, N1, N2, b, p=0):
+            ctx.cfg = (N1, N2, b, p)
+            return fft(x, N1, N2, b, p, dir=-1)
+
+        @staticmethod
+        def backward(ctx, g):
+            N1, N2, b, p = ctx.cfg
+            return fft(g.contiguous(), N1, N2, b, p, dir=+1), None, None, None, None
+except ImportError:  # pragma: no cover - torch is a hard requirement on the GPU machine
+    PacoFFT = None

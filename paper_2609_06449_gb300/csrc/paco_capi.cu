@@ -1,0 +1,471 @@
+// paco_capi.cu -- host side of the C ABI declared in include/paco.h.
+//
+// Plan construction (legality per Sect. 2, Eq. exact-divisibility; tile and
+// cluster choice; FP64 twiddle tables generated on the device), execution
+// (two stage launches per Theorem 3's composition, Eq. (10)), the unfused
+// three-pass form, the host-buffer form, and error reporting.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/paco.h"
+#include "paco_common.cuh"
+#include "paco_stage.cuh"
+
+namespace paco {
+const void *stage_kernel_fn_f32(int lgL);
+const void *stage_kernel_fn_f64(int lgL);
+} // namespace paco
+
+using namespace paco;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+static paco_status_t fail(paco_status_t st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define PACO_CUDA_TRY(call)                                                              \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(PACO_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+extern "C" const char *paco_last_error(void) { return g_last_error.c_str(); }
+extern "C" const char *paco_version(void) { return "paco-gb300 0.1"; }
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+struct StageCfg {
+    int lgL = 0;      // log2 of the transform length of this stage
+    int lgW = 0;      // log2 tile width
+    int lgK = 0;      // log2 cluster size
+    int threads = 0;
+    int smem = 0;     // dynamic shared memory, bytes
+    int ntiles = 0;   // column tiles per transform
+    const void *fn = nullptr;
+};
+
+struct paco_plan {
+    int64_t N1 = 0, N2 = 0, N = 0, batch = 0;
+    int b = 0, t = 0, p = 0, m1 = 0, m2 = 0;
+    paco_dtype_t dtype = PACO_C64;
+    int esize = 8;                 // bytes per complex element
+    int device = 0;
+    StageCfg st[2];                // stage 1 (L = N1, C = N2), stage 2 (L = N2, C = N1)
+    StageCfg ph1;                  // Phase I alone (mode 3), same geometry as st[0]
+    void *twL1 = nullptr, *twL2 = nullptr, *twN_lo = nullptr, *twN_hi = nullptr;
+    int twN_lo_bits = 0;
+    int *d_status = nullptr;
+};
+
+static int ilog2_exact(int64_t v)
+{
+    if (v <= 0 || (v & (v - 1))) return -1;
+    int l = 0;
+    while ((int64_t(1) << l) < v) ++l;
+    return l;
+}
+
+// w_M^{-(r*mult)} for r in [count], generated in FP64 with sincospi.
+template <typename R>
+__global__ void twiddle_gen_kernel(cx<R> *out, long long M, long long count, long long mult)
+{
+    long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= count) return;
+    long long e = (r * mult) % M;
+    double s, c;
+    sincospi(2.0 * (double)e / (double)M, &s, &c);
+    out[r] = make_cx<R>((R)c, (R)(-s));
+}
+
+static paco_status_t gen_table(paco_plan *pl, void **dst, long long M, long long count,
+                               long long mult)
+{
+    size_t bytes = (size_t)count * (size_t)pl->esize;
+    PACO_CUDA_TRY(cudaMalloc(dst, bytes));
+    int threads = 256;
+    long long blocks = (count + threads - 1) / threads;
+    if (pl->esize == 8)
+        twiddle_gen_kernel<float><<<(unsigned)blocks, threads>>>((cx<float> *)*dst, M, count, mult);
+    else
+        twiddle_gen_kernel<double><<<(unsigned)blocks, threads>>>((cx<double> *)*dst, M, count, mult);
+    PACO_CUDA_TRY(cudaGetLastError());
+    return PACO_OK;
+}
+
+// Tile width W and cluster size K for a stage of length 2^lgL over C columns:
+// about 64 KiB of tile per CTA, at least 32 B per row segment.
+static void choose_tile(const paco_plan *pl, int lgL, int64_t C, int req_w, int req_k,
+                        int *lgW_out, int *lgK_out)
+{
+    const int lgE = pl->esize == 8 ? 3 : 4;
+    const int lgBudget = 16 - lgE;                   // elements per CTA: 8192 (c64) / 4096 (c128)
+    int lgC = ilog2_exact(C);
+    int lgW;
+    if (req_w > 0) lgW = ilog2_exact(req_w);
+    else {
+        int lgWmin = 5 - lgE;                        // 32-byte rows: 4 (c64) / 2 (c128)
+        lgW = lgBudget - lgL;
+        if (lgW < lgWmin) lgW = lgWmin;
+        if (lgW > 4) lgW = 4;                        // at most 16 columns
+    }
+    if (lgW > lgC) lgW = lgC;
+    if (lgW < 0) lgW = 0;
+    int lgK;
+    if (req_k > 0) lgK = ilog2_exact(req_k);
+    else {
+        lgK = lgL + lgW - lgBudget;
+        if (lgK < 0) lgK = 0;
+    }
+    // the cluster splits both factors of L
+    int lgB = lgL / 2;
+    if (lgK > lgB) lgK = lgB;
+    *lgW_out = lgW;
+    *lgK_out = lgK;
+}
+
+static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode,
+                                 int req_w, int req_k)
+{
+    sc->lgL = lgL;
+    choose_tile(pl, lgL, C, req_w, req_k, &sc->lgW, &sc->lgK);
+    if (sc->lgW < 0 || sc->lgK < 0 || sc->lgK > 3)
+        return fail(PACO_ERR_INVALID_ARG, "tile width / cluster size must be powers of two, cluster <= 8");
+    const int A = 1 << ((lgL + 1) / 2), B = 1 << (lgL / 2);
+    const int W = 1 << sc->lgW, K = 1 << sc->lgK;
+    if ((int64_t)W > C) return fail(PACO_ERR_INVALID_ARG, "tile width %d exceeds %lld columns", W, (long long)C);
+    if (K > 1 && (A % K || B % K)) return fail(PACO_ERR_INVALID_ARG, "cluster %d does not divide the split %dx%d", K, A, B);
+    const int L = 1 << lgL;
+    const int EPT = L < 16 ? L : 16;
+    const int64_t NE = (int64_t)A * (B / K) * W;     // elements per CTA
+    sc->ntiles = (int)(C / W);
+    sc->fn = (pl->esize == 8) ? stage_kernel_fn_f32(lgL) : stage_kernel_fn_f64(lgL);
+    if (!sc->fn) return fail(PACO_ERR_UNSUPPORTED, "stage length 2^%d is not built (max 2^14)", lgL);
+    if (B == 1) {
+        sc->threads = W;
+        sc->smem = 0;
+    } else {
+        if (NE % EPT) return fail(PACO_ERR_INVALID_ARG, "tile too small");
+        sc->threads = (int)(NE / EPT);
+        const int pad = (mode == 1) ? 1 : W;
+        sc->smem = stage_smem_elems(A, B, K, W, pad) * pl->esize;
+    }
+    if (sc->threads > 512 || sc->threads < 1)
+        return fail(PACO_ERR_INVALID_ARG, "tile of %lld elements needs %d threads (max 512)",
+                    (long long)NE, sc->threads);
+    if (sc->smem > 227 * 1024)
+        return fail(PACO_ERR_INVALID_ARG, "tile needs %d bytes of shared memory (max 227 KiB)", sc->smem);
+    PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       227 * 1024));
+    return PACO_OK;
+}
+
+static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
+{
+    *out = nullptr;
+    if (!o) return fail(PACO_ERR_INVALID_ARG, "opts is NULL");
+    if (o->b != 2 && o->b != 4 && o->b != 8 && o->b != 16)
+        return fail(PACO_ERR_INVALID_ARG, "radix b=%d must be 2, 4, 8 or 16", o->b);
+    if (o->dtype != PACO_C64 && o->dtype != PACO_C128)
+        return fail(PACO_ERR_UNSUPPORTED, "dtype %d is not built", (int)o->dtype);
+    if (o->batch < 0) return fail(PACO_ERR_INVALID_ARG, "batch %lld < 0", (long long)o->batch);
+    const int t = ilog2_exact(o->b);
+    const int l1 = ilog2_exact(o->N1), l2 = ilog2_exact(o->N2);
+    if (l1 < 1 || l1 % t) return fail(PACO_ERR_INVALID_ARG, "N1=%lld is not a power of b=%d (>= b)", (long long)o->N1, o->b);
+    if (l2 < 1 || l2 % t) return fail(PACO_ERR_INVALID_ARG, "N2=%lld is not a power of b=%d (>= b)", (long long)o->N2, o->b);
+    if (l1 + l2 > 32) return fail(PACO_ERR_UNSUPPORTED, "N = 2^%d exceeds 2^32", l1 + l2);
+    if (l1 > 14 || l2 > 14) return fail(PACO_ERR_UNSUPPORTED, "factors above 2^14 are not built");
+    const int m1 = l1 / t, m2 = l2 / t;
+    int p = o->p;
+    if (p == 0) {
+        int e = (m1 < m2 ? m1 : m2) / 2;
+        if (e < 1) e = 1;
+        p = 1 << (t * e);
+    }
+    const int lp = ilog2_exact(p);
+    if (p < 2 || lp < 0 || lp % t || p > o->N1 || p > o->N2 || o->N1 % p || o->N2 % p)
+        return fail(PACO_ERR_INVALID_ARG, "p=%d must be a power of b=%d with 2 <= p, p | N1, p | N2", p, o->b);
+
+    paco_plan *pl = new (std::nothrow) paco_plan();
+    if (!pl) return fail(PACO_ERR_NOMEM, "out of host memory");
+    pl->N1 = o->N1; pl->N2 = o->N2; pl->N = o->N1 * o->N2; pl->batch = o->batch;
+    pl->b = o->b; pl->t = t; pl->p = p; pl->m1 = m1; pl->m2 = m2;
+    pl->dtype = o->dtype;
+    pl->esize = (o->dtype == PACO_C128) ? 16 : 8;
+    cudaGetDevice(&pl->device);
+
+    paco_status_t st;
+    if ((st = setup_stage(pl, &pl->st[0], l1, pl->N2, 1, o->tile_w, o->cluster)) != PACO_OK ||
+        (st = setup_stage(pl, &pl->ph1, l1, pl->N2, 3, o->tile_w, o->cluster)) != PACO_OK ||
+        (st = setup_stage(pl, &pl->st[1], l2, pl->N1, 2, o->tile_w, o->cluster)) != PACO_OK) {
+        delete pl;
+        return st;
+    }
+    // FP64-generated twiddle tables: w_N1^{-r}, w_N2^{-r}, and w_N^{-r} in
+    // two levels (r = hi * 2^h + lo).
+    const int lgN = l1 + l2;
+    pl->twN_lo_bits = (lgN + 1) / 2;
+    const long long nlo = 1LL << pl->twN_lo_bits, nhi = (1LL << lgN) / nlo;
+    if ((st = gen_table(pl, &pl->twL1, pl->N1, pl->N1, 1)) != PACO_OK ||
+        (st = gen_table(pl, &pl->twL2, pl->N2, pl->N2, 1)) != PACO_OK ||
+        (st = gen_table(pl, &pl->twN_lo, pl->N, nlo, 1)) != PACO_OK ||
+        (st = gen_table(pl, &pl->twN_hi, pl->N, nhi, nlo)) != PACO_OK) {
+        paco_plan_destroy(pl);
+        return st;
+    }
+    cudaError_t e = cudaMalloc(&pl->d_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        paco_plan_destroy(pl);
+        return fail(PACO_ERR_CUDA, "plan setup: %s", cudaGetErrorString(e));
+    }
+    *out = pl;
+    return PACO_OK;
+}
+
+extern "C" paco_status_t paco_plan_create_ex(paco_plan_t **out, const paco_plan_opts_t *opts)
+{
+    if (!out) return fail(PACO_ERR_INVALID_ARG, "out is NULL");
+    return plan_build(out, opts);
+}
+
+extern "C" paco_plan_t *paco_plan_create(int64_t N1, int64_t N2, int b, int64_t batch,
+                                         paco_dtype_t dtype)
+{
+    paco_plan_opts_t o;
+    memset(&o, 0, sizeof(o));
+    o.N1 = N1; o.N2 = N2; o.b = b; o.batch = batch; o.dtype = dtype;
+    paco_plan *pl = nullptr;
+    plan_build(&pl, &o);
+    return pl;
+}
+
+extern "C" void paco_plan_destroy(paco_plan_t *pl)
+{
+    if (!pl) return;
+    cudaFree(pl->twL1);
+    cudaFree(pl->twL2);
+    cudaFree(pl->twN_lo);
+    cudaFree(pl->twN_hi);
+    cudaFree(pl->d_status);
+    delete pl;
+}
+
+extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t *info)
+{
+    if (!pl || !info) return fail(PACO_ERR_INVALID_ARG, "NULL argument");
+    memset(info, 0, sizeof(*info));
+    info->N1 = pl->N1; info->N2 = pl->N2; info->N = pl->N; info->batch = pl->batch;
+    info->b = pl->b; info->p = pl->p; info->m1 = pl->m1; info->m2 = pl->m2;
+    info->dtype = pl->dtype;
+    const int64_t line = 128 / pl->esize;
+    info->slab_width_ok = (pl->N1 / pl->p >= line) && (pl->N2 / pl->p >= line);
+    const int64_t p = pl->p;
+    info->items_per_pair = pl->N / (p * p);
+    info->h = pl->N / p - pl->N / (p * p);
+    info->mu = pl->N - pl->N / p;
+    for (int s = 0; s < 2; ++s) {
+        info->stage_tile_w[s] = 1 << pl->st[s].lgW;
+        info->stage_cluster[s] = 1 << pl->st[s].lgK;
+        info->stage_threads[s] = pl->st[s].threads;
+        info->stage_smem[s] = pl->st[s].smem;
+    }
+    return PACO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// execution
+// ---------------------------------------------------------------------------
+static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int mode,
+                                  const void *in, void *out, int dir, cudaStream_t stream)
+{
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.batch_stride = pl->N;
+    a.lgW = sc.lgW;
+    a.lgK = sc.lgK;
+    a.mode = mode;
+    a.rev_t = pl->t;
+    a.conj = (dir == 1);
+    a.N_mask = (unsigned)(pl->N - 1);
+    a.twN_lo = pl->twN_lo;
+    a.twN_hi = pl->twN_hi;
+    a.twN_lo_bits = pl->twN_lo_bits;
+    a.pad = (mode == 1) ? 1 : (1 << sc.lgW);
+    if (mode == 1 || mode == 3) {         // over the input view: L = N1, C = N2
+        a.C = (int)pl->N2;
+        a.twL = pl->twL1;
+        if (mode == 1) { a.out_ld = (int)pl->N1; a.rev_bits = pl->m2 * pl->t; }
+        else { a.out_ld = (int)pl->N2; a.rev_bits = pl->m1 * pl->t; }
+    } else {                              // over W: L = N2, C = N1
+        a.C = (int)pl->N1;
+        a.twL = pl->twL2;
+        a.out_ld = (int)pl->N1;
+        a.rev_bits = pl->m2 * pl->t;
+    }
+    const int K = 1 << sc.lgK;
+    for (int64_t b0 = 0; b0 < pl->batch; b0 += 65535) {
+        const int64_t nb = (pl->batch - b0 < 65535) ? pl->batch - b0 : 65535;
+        StageArgs ab = a;
+        ab.in = (const char *)in + (size_t)(b0 * pl->N) * pl->esize;
+        ab.out = (char *)out + (size_t)(b0 * pl->N) * pl->esize;
+        cudaLaunchConfig_t cfg;
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3((unsigned)(sc.ntiles * K), (unsigned)nb, 1);
+        cfg.blockDim = dim3((unsigned)sc.threads, 1, 1);
+        cfg.dynamicSmemBytes = (size_t)sc.smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)K;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        void *params[] = {&ab};
+        PACO_CUDA_TRY(cudaLaunchKernelExC(&cfg, sc.fn, params));
+    }
+    return PACO_OK;
+}
+
+static bool overlap(const void *a, const void *b, size_t bytes)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + bytes && y < x + bytes;
+}
+
+static paco_status_t check_exec(const paco_plan *pl, const void *in, const void *out, int dir,
+                                bool allow_inplace)
+{
+    if (!pl) return fail(PACO_ERR_INVALID_ARG, "plan is NULL");
+    if (dir != -1 && dir != 1) return fail(PACO_ERR_INVALID_ARG, "dir=%d must be -1 or +1", dir);
+    if (pl->batch == 0) return PACO_OK;
+    if (!in || !out) return fail(PACO_ERR_INVALID_ARG, "NULL buffer");
+    if (((uintptr_t)in | (uintptr_t)out) & 15u)
+        return fail(PACO_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    const size_t bytes = (size_t)(pl->N * pl->batch) * pl->esize;
+    if (overlap(in, out, bytes) && !(allow_inplace && in == out))
+        return fail(PACO_ERR_ALIASING, "input and output overlap");
+    return PACO_OK;
+}
+
+static void set_device(const paco_plan *pl)
+{
+    int d = -1;
+    cudaGetDevice(&d);
+    if (d != pl->device) cudaSetDevice(pl->device);
+}
+
+extern "C" paco_status_t paco_execute(paco_plan_t *pl, const void *in, void *out, int dir,
+                                      paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, in, out, dir, false);
+    if (st != PACO_OK || pl->batch == 0) return st;
+    set_device(pl);
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s)) != PACO_OK) return st;
+    return launch_stage(pl, pl->st[1], 2, out, out, dir, s);
+}
+
+extern "C" paco_status_t paco_execute_stage1(paco_plan_t *pl, const void *in, void *W, int dir,
+                                             paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, in, W, dir, false);
+    if (st != PACO_OK || pl->batch == 0) return st;
+    set_device(pl);
+    return launch_stage(pl, pl->st[0], 1, in, W, dir, (cudaStream_t)stream);
+}
+
+extern "C" paco_status_t paco_execute_stage2(paco_plan_t *pl, const void *W, void *out, int dir,
+                                             paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, W, out, dir, true);
+    if (st != PACO_OK || pl->batch == 0) return st;
+    set_device(pl);
+    return launch_stage(pl, pl->st[1], 2, W, out, dir, (cudaStream_t)stream);
+}
+
+extern "C" paco_status_t paco_execute_phase1(paco_plan_t *pl, const void *in, void *out, int dir,
+                                             paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, in, out, dir, false);
+    if (st != PACO_OK || pl->batch == 0) return st;
+    set_device(pl);
+    return launch_stage(pl, pl->ph1, 3, in, out, dir, (cudaStream_t)stream);
+}
+
+extern "C" paco_status_t paco_permute(paco_plan_t *pl, const void *A_tilde, void *W, int dir,
+                                      paco_stream_t stream)
+{
+    (void)pl; (void)A_tilde; (void)W; (void)dir; (void)stream;
+    return fail(PACO_ERR_UNSUPPORTED, "paco_permute is not built yet");
+}
+
+extern "C" paco_status_t paco_execute_host(paco_plan_t *pl, const void *h_in, void *h_out,
+                                           void *d_in, void *d_out, int dir, paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, d_in, d_out, dir, false);
+    if (st != PACO_OK || pl->batch == 0) return st;
+    if (!h_in || !h_out) return fail(PACO_ERR_INVALID_ARG, "NULL host buffer");
+    set_device(pl);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)(pl->N * pl->batch) * pl->esize;
+    PACO_CUDA_TRY(cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, s));
+    if ((st = paco_execute(pl, d_in, d_out, dir, stream)) != PACO_OK) return st;
+    PACO_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, s));
+    return PACO_OK;
+}
+
+extern "C" paco_status_t paco_plan_check(paco_plan_t *pl)
+{
+    if (!pl) return fail(PACO_ERR_INVALID_ARG, "plan is NULL");
+    set_device(pl);
+    PACO_CUDA_TRY(cudaDeviceSynchronize());
+    int h = 0;
+    PACO_CUDA_TRY(cudaMemcpy(&h, pl->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    PACO_CUDA_TRY(cudaMemset(pl->d_status, 0, sizeof(int)));
+    if (h == PACO_ERR_TIMEOUT) return fail(PACO_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (h != 0) return fail(PACO_ERR_DEVICE, "device status word %d", h);
+    return PACO_OK;
+}
+
+extern "C" int64_t paco_digit_reverse(int64_t u, int b, int ell)
+{
+    int t = ilog2_exact(b);
+    if (t < 1 || t > 4 || ell < 0 || (int64_t)ell * t > 31) return -1;
+    const int bits = ell * t;
+    if (u < 0 || u >= (int64_t(1) << bits)) return -1;
+    if (bits == 0) return 0;
+    // same construction as the device map: reverse all bits, then restore the
+    // bit order inside every t-bit digit
+    uint32_t x = 0, v = (uint32_t)u;
+    for (int i = 0; i < bits; ++i) x |= ((v >> i) & 1u) << (bits - 1 - i);
+    uint32_t y = 0;
+    for (int d = 0; d < ell; ++d) {
+        uint32_t dig = (x >> (d * t)) & ((1u << t) - 1u);
+        uint32_t r = 0;
+        for (int i = 0; i < t; ++i) r |= ((dig >> i) & 1u) << (t - 1 - i);
+        y |= r << (d * t);
+    }
+    return (int64_t)y;
+}

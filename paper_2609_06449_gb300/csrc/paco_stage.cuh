@@ -1,0 +1,387 @@
+// paco_stage.cuh -- one PACO local-FFT stage as a CUDA kernel template.
+//
+// A stage computes a length-L DFT down every column of a row-major matrix
+// (L rows, C columns), tile by tile:
+//
+//   mode 1  Phase I fused with the middle stage (Sect. 4.2): column DFTs of
+//           the input view X[j1, j2] = x[j1*N2 + j2] (L = N1, C = N2), then
+//           the top-level twiddle w_N^{-k1 c} (Eq. two-factor-ct; applied from
+//           the logical coordinates, App. C.2 "application to twiddle
+//           multiplication"), stored to W[pi_m2(c)][k1]: the full digit
+//           reversal pi_m(a ++ c) = pi_m2(c) ++ pi_m1(a)
+//           (Eq. full-middle-digit-reversal) resolved in the store address.
+//   mode 2  Phase III (input-layout operator B_m2 = Omega P_pi, Lemma 1):
+//           column v of W is read through the digit-reversed row map
+//           j -> pi_m2(j) and its DFT is stored in natural order to
+//           out[k2][v] (L = N2, C = N1).
+//   mode 3  Phase I alone (A_m1 = P_pi Omega, Lemma 1): stored to
+//           A-tilde[pi_m1(k1)][c], no twiddle (for the unfused pipeline).
+//
+// Inside a tile the length-L transform is split once, Cooley-Tukey style,
+// as L = A*B with the balanced digit split of the paper's scheduler
+// (A = 2^ceil(l/2), B = 2^floor(l/2); Sect. 4.1): j = j_hi*B + j_lo,
+// k = k_lo + A*k_hi.
+//
+//   F1  A-point DFTs over j_hi for every (j_lo, column)  -> k_lo
+//   tw  w_L^{-k_lo j_lo}  (the layout-aware twiddle, Eq. twop)
+//   F2  B-point DFTs over j_lo for every (k_lo, column)  -> k_hi
+//
+// F1 and F2 each take one or two in-register radix passes (radix <= 16)
+// with a shared-memory exchange between them.  A tile of W columns spans a
+// thread-block cluster of K CTAs: CTA `rank` loads the j_lo range
+// [rank*B/K, (rank+1)*B/K) and, after F1, sends each k_lo to the CTA that
+// owns it (k_lo / (A/K)) through distributed shared memory -- the batch
+// split of the paper's scheduler mapped onto the cluster.  Each thread holds
+// EPT = min(16, L) elements.  Nothing is written to global memory except the
+// stage output; no scratch.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "paco_common.cuh"
+
+namespace paco {
+
+namespace cg = cooperative_groups;
+
+template <int X>
+struct ilog2c { static constexpr int value = 1 + ilog2c<X / 2>::value; };
+template <>
+struct ilog2c<1> { static constexpr int value = 0; };
+
+template <typename R>
+__device__ __forceinline__ cx<R> ldg_cx(const cx<R> *p);
+template <>
+__device__ __forceinline__ cx<float> ldg_cx<float>(const cx<float> *p)
+{
+    float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+    return make_cx<float>(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<double> ldg_cx<double>(const cx<double> *p)
+{
+    double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+    return make_cx<double>(v.x, v.y);
+}
+
+template <typename R>
+__device__ __forceinline__ void st_cx(cx<R> *p, cx<R> v) { *p = v; }
+
+// Dynamic shared memory needed by a stage CTA (elements of cx<R>).
+__host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int pad)
+{
+    const int L = A * B;
+    int lg = 0;
+    while ((1 << lg) < L) ++lg;
+    const int SL = 1 << ((lg + 1) / 2), SH = L / SL;
+    const int Ak = A / K, Bk = B / K;
+    const int P2 = B * W + pad;
+    const int P1 = (K == 1) ? P2 : Bk * W;
+    const int data = (A * P1 > Ak * P2) ? A * P1 : Ak * P2;
+    return data + A + B + SL + SH + Ak * W + B * W;
+}
+
+template <typename R, int A, int B>
+__global__ void __launch_bounds__(512) paco_stage_kernel(const StageArgs args)
+{
+    using C = cx<R>;
+    constexpr int L = A * B;
+    constexpr int EPT = L < 16 ? L : 16;          // elements per thread
+    constexpr int RA1 = A >= 16 ? 16 : A;         // F1 radices
+    constexpr int RA2 = A / RA1;
+    constexpr int RB1 = B >= 16 ? 16 : B;         // F2 radices
+    constexpr int RB2 = B / RB1;
+    constexpr int LGL = ilog2c<L>::value;
+    constexpr int LG_SL = (LGL + 1) / 2;
+    constexpr int SL = 1 << LG_SL, SH = L / SL;
+    static_assert(B >= 2, "B == 1 takes paco_stage_kernel_b1");
+    static_assert(EPT % RA1 == 0 && EPT % RB1 == 0, "radix must divide EPT");
+    static_assert(RA2 == 1 || EPT % RA2 == 0, "radix must divide EPT");
+    static_assert(RB2 == 1 || EPT % RB2 == 0, "radix must divide EPT");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const int lgW = args.lgW, lgK = args.lgK;
+    const int W = 1 << lgW, K = 1 << lgK;
+    const int Bk = B >> lgK, Ak = A >> lgK;
+    const int S1 = Bk << lgW;                     // F1 sequences per CTA
+    const int P2 = (B << lgW) + args.pad;         // F2 row stride
+    const int P1 = (K == 1) ? P2 : S1;            // F1 row stride
+    const int NT = blockDim.x;
+    const int mode = args.mode;
+
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int data_elems = (A * P1 > Ak * P2) ? A * P1 : Ak * P2;
+    C *twA = sm + data_elems;     // w_A^{-r}, r < A
+    C *twB = twA + A;             // w_B^{-r}, r < B
+    C *tlo = twB + B;             // w_L^{-r}, r < SL
+    C *thi = tlo + SL;            // w_L^{-r*SL}, r < SH
+    C *E1 = thi + SH;             // mode 1: w_N^{-k_lo c}     [Ak][W]
+    C *E2 = E1 + Ak * W;          // mode 1: w_N^{-A k_hi c}   [B][W]
+
+    const int tid = threadIdx.x;
+    int rank = 0;
+    if (K > 1) rank = (int)cg::this_cluster().block_rank();
+    const int tile = blockIdx.x >> lgK;
+    const long long boff = (long long)blockIdx.y * args.batch_stride;
+    const int c0 = tile << lgW;
+    const R csign = args.conj ? R(-1) : R(1);
+
+    // ---- per-CTA twiddle tables (all forward, from FP64-generated tables)
+    {
+        const C *twL = reinterpret_cast<const C *>(args.twL);
+        for (int r = tid; r < A; r += NT) twA[r] = ldg_cx(twL + r * B);
+        for (int r = tid; r < B; r += NT) twB[r] = ldg_cx(twL + r * A);
+        for (int r = tid; r < SL; r += NT) tlo[r] = ldg_cx(twL + r);
+        for (int r = tid; r < SH; r += NT) thi[r] = ldg_cx(twL + r * SL);
+        if (mode == 1) {
+            const C *nlo = reinterpret_cast<const C *>(args.twN_lo);
+            const C *nhi = reinterpret_cast<const C *>(args.twN_hi);
+            const unsigned lomask = (1u << args.twN_lo_bits) - 1u;
+            const int nE1 = Ak << lgW, nE = nE1 + (B << lgW);
+            for (int e = tid; e < nE; e += NT) {
+                unsigned r;
+                if (e < nE1) {
+                    const unsigned klo = (unsigned)(rank * Ak + (e >> lgW));
+                    const unsigned c = (unsigned)(c0 + (e & (W - 1)));
+                    r = (klo * c) & args.N_mask;
+                } else {
+                    const int e2 = e - nE1;
+                    const unsigned khi = (unsigned)(e2 >> lgW);
+                    const unsigned c = (unsigned)(c0 + (e2 & (W - 1)));
+                    r = ((unsigned)A * khi * c) & args.N_mask;
+                }
+                E1[e] = cmul(ldg_cx(nlo + (r & lomask)), ldg_cx(nhi + (r >> args.twN_lo_bits)));
+            }
+        }
+    }
+    __syncthreads();
+
+    C v[EPT];
+    const C *gin = reinterpret_cast<const C *>(args.in) + boff;
+
+    // ---- F1 pass 1: radix RA1 over j_hi, span RA2; operands straight from HBM
+    {
+        constexpr int NB = EPT / RA1;
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            const int bfi = tid + NT * u;
+            const int seq = bfi & (S1 - 1), jj = bfi / S1;
+            const int jl = seq >> lgW, col = seq & (W - 1);
+            const int jlo = rank * Bk + jl;
+#pragma unroll
+            for (int r = 0; r < RA1; ++r) {
+                const int j = (jj + RA2 * r) * B + jlo;       // logical row in [L]
+                const unsigned row = (mode == 2) ? digit_reverse((unsigned)j, args.rev_bits, args.rev_t)
+                                                 : (unsigned)j;
+                C x = ldg_cx(gin + (long long)row * args.C + c0 + col);
+                x.y *= csign;
+                v[u * RA1 + r] = x;
+            }
+            dft<RA1>(v + u * RA1);
+            if constexpr (RA2 > 1) {
+#pragma unroll
+                for (int s = 1; s < RA1; ++s)
+                    v[u * RA1 + s] = cmul(v[u * RA1 + s], twA[s * jj]);   // w_A^{-s jj}
+#pragma unroll
+                for (int s = 0; s < RA1; ++s)
+                    sm[(jj + RA2 * s) * P1 + seq] = v[u * RA1 + s];
+            }
+        }
+    }
+
+    // ---- F1 pass 2 (if A > 16): radix RA2 over the span, groups g < 16.
+    // After F1 the thread's element (u, k) has k_lo = kl_of(u, k).
+    constexpr int RF = (RA2 > 1) ? RA2 : RA1;     // radix of F1's last pass
+    constexpr int NBF = EPT / RF;
+    if constexpr (RA2 > 1) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NBF; ++u) {
+            const int bfi = tid + NT * u;
+            const int seq = bfi & (S1 - 1), g = bfi / S1;
+#pragma unroll
+            for (int r = 0; r < RA2; ++r) v[u * RA2 + r] = sm[(g * RA2 + r) * P1 + seq];
+            dft<RA2>(v + u * RA2);
+        }
+    }
+
+    // ---- twiddle w_L^{-k_lo j_lo}, then hand each k_lo to its owner
+    if (K == 1) __syncthreads();                  // all F1 reads done before reuse
+#pragma unroll
+    for (int u = 0; u < NBF; ++u) {
+        const int bfi = tid + NT * u;
+        const int seq = bfi & (S1 - 1), hi = bfi / S1;   // hi = g (2 passes) or 0
+        const int jl = seq >> lgW, col = seq & (W - 1);
+        const int jlo = rank * Bk + jl;
+#pragma unroll
+        for (int k = 0; k < RF; ++k) {
+            const int klo = (RA2 > 1) ? (hi + RA1 * k) : k;
+            const unsigned r = (unsigned)(klo * jlo);     // < L
+            C t = cmul(tlo[r & (SL - 1)], thi[r >> LG_SL]);
+            v[u * RF + k] = cmul(v[u * RF + k], t);
+        }
+    }
+    if (K == 1) {
+        // natural k_lo order in place of the F1 layout: sm[k_lo][j_lo][col]
+#pragma unroll
+        for (int u = 0; u < NBF; ++u) {
+            const int bfi = tid + NT * u;
+            const int seq = bfi & (S1 - 1), hi = bfi / S1;
+#pragma unroll
+            for (int k = 0; k < RF; ++k) {
+                const int klo = (RA2 > 1) ? (hi + RA1 * k) : k;
+                sm[klo * P2 + seq] = v[u * RF + k];
+            }
+        }
+        __syncthreads();
+    } else {
+        cg::cluster_group cluster = cg::this_cluster();
+        cluster.sync();                           // every CTA finished reading its F1 data
+        const int lgAk = ilog2c<A>::value - lgK;
+#pragma unroll
+        for (int u = 0; u < NBF; ++u) {
+            const int bfi = tid + NT * u;
+            const int seq = bfi & (S1 - 1), hi = bfi / S1;
+            const int jl = seq >> lgW, col = seq & (W - 1);
+            const int jlo = rank * Bk + jl;
+#pragma unroll
+            for (int k = 0; k < RF; ++k) {
+                const int klo = (RA2 > 1) ? (hi + RA1 * k) : k;
+                const int dst = klo >> lgAk, al = klo & (Ak - 1);
+                C *p = cluster.map_shared_rank(sm + al * P2 + (jlo << lgW) + col, dst);
+                *p = v[u * RF + k];
+            }
+        }
+        cluster.sync();                           // all of this CTA's F2 input has landed
+    }
+
+    // ---- F2 pass 1: radix RB1 over j_lo, span RB2
+    constexpr int NB1 = EPT / RB1;
+    C *gout = reinterpret_cast<C *>(args.out) + boff;
+#pragma unroll
+    for (int u = 0; u < NB1; ++u) {
+        const int bfi = tid + NT * u;
+        const int col = bfi & (W - 1);
+        const int jj = (bfi >> lgW) % RB2;
+        const int al = (bfi >> lgW) / RB2;
+#pragma unroll
+        for (int r = 0; r < RB1; ++r) v[u * RB1 + r] = sm[al * P2 + ((jj + RB2 * r) << lgW) + col];
+        dft<RB1>(v + u * RB1);
+        if constexpr (RB2 > 1) {
+#pragma unroll
+            for (int s = 1; s < RB1; ++s) v[u * RB1 + s] = cmul(v[u * RB1 + s], twB[s * jj]);
+#pragma unroll
+            for (int s = 0; s < RB1; ++s) sm[al * P2 + ((jj + RB2 * s) << lgW) + col] = v[u * RB1 + s];
+        }
+    }
+
+    // ---- F2 pass 2 (if B > 16) and the store
+    constexpr int RL = (RB2 > 1) ? RB2 : RB1;    // radix of the last pass
+    constexpr int NBL = EPT / RL;
+    if constexpr (RB2 > 1) __syncthreads();
+#pragma unroll
+    for (int u = 0; u < NBL; ++u) {
+        const int bfi = tid + NT * u;
+        int al, col, hi;
+        if constexpr (RB2 > 1) {
+            if (mode == 1) {
+                al = bfi & (Ak - 1);
+                col = (bfi / Ak) & (W - 1);
+                hi = bfi / (Ak << lgW);
+            } else {
+                col = bfi & (W - 1);
+                al = (bfi >> lgW) & (Ak - 1);
+                hi = (bfi >> lgW) / Ak;
+            }
+#pragma unroll
+            for (int r = 0; r < RB2; ++r) v[u * RB2 + r] = sm[al * P2 + ((hi * RB2 + r) << lgW) + col];
+            dft<RB2>(v + u * RB2);
+        } else {
+            // single F2 pass: the registers already hold the outputs of
+            // butterfly (col, jj = 0, al)
+            col = bfi & (W - 1);
+            al = bfi >> lgW;
+            hi = 0;
+        }
+        const int klo = rank * Ak + al;
+        const int c = c0 + col;
+#pragma unroll
+        for (int k = 0; k < RL; ++k) {
+            const int khi = (RB2 > 1) ? (hi + RB1 * k) : k;
+            const int kk = klo + A * khi;             // natural frequency in [L]
+            C y = v[u * RL + k];
+            long long idx;
+            if (mode == 1) {
+                y = cmul(y, cmul(E1[(al << lgW) + col], E2[(khi << lgW) + col]));
+                const unsigned urow = digit_reverse((unsigned)c, args.rev_bits, args.rev_t);
+                idx = (long long)urow * args.out_ld + kk;
+            } else if (mode == 2) {
+                idx = (long long)kk * args.out_ld + c;
+            } else {
+                const unsigned arow = digit_reverse((unsigned)kk, args.rev_bits, args.rev_t);
+                idx = (long long)arow * args.out_ld + c;
+            }
+            y.y *= csign;
+            st_cx(gout + idx, y);
+        }
+    }
+}
+
+// L = A (B == 1): the whole transform is F1; store straight from F1's layout.
+// Only tiny sizes take this path (L = 2).
+template <typename R, int A>
+__global__ void __launch_bounds__(512) paco_stage_kernel_b1(const StageArgs args)
+{
+    using C = cx<R>;
+    static_assert(A <= 16, "single-factor path is for tiny transforms");
+    constexpr int EPT = A;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    (void)smem_raw;
+    const int lgW = args.lgW;
+    const int W = 1 << lgW;
+    const int NT = blockDim.x;
+    const int tile = blockIdx.x;
+    const long long boff = (long long)blockIdx.y * args.batch_stride;
+    const int c0 = tile << lgW;
+    const R csign = args.conj ? R(-1) : R(1);
+    const C *gin = reinterpret_cast<const C *>(args.in) + boff;
+    C *gout = reinterpret_cast<C *>(args.out) + boff;
+    const int tid = threadIdx.x;
+    if (tid >= W) return;
+    (void)NT;
+    const int col = tid, c = c0 + col;
+    C v[EPT];
+#pragma unroll
+    for (int r = 0; r < A; ++r) {
+        const unsigned row = (args.mode == 2) ? digit_reverse((unsigned)r, args.rev_bits, args.rev_t)
+                                              : (unsigned)r;
+        C x = ldg_cx(gin + (long long)row * args.C + c);
+        x.y *= csign;
+        v[r] = x;
+    }
+    dft<A>(v);
+    const C *nlo = reinterpret_cast<const C *>(args.twN_lo);
+    const C *nhi = reinterpret_cast<const C *>(args.twN_hi);
+#pragma unroll
+    for (int k = 0; k < A; ++k) {
+        C y = v[k];
+        long long idx;
+        if (args.mode == 1) {
+            const unsigned r = ((unsigned)k * (unsigned)c) & args.N_mask;
+            y = cmul(y, cmul(ldg_cx(nlo + (r & ((1u << args.twN_lo_bits) - 1u))),
+                             ldg_cx(nhi + (r >> args.twN_lo_bits))));
+            const unsigned urow = digit_reverse((unsigned)c, args.rev_bits, args.rev_t);
+            idx = (long long)urow * args.out_ld + k;
+        } else if (args.mode == 2) {
+            idx = (long long)k * args.out_ld + c;
+        } else {
+            const unsigned arow = digit_reverse((unsigned)k, args.rev_bits, args.rev_t);
+            idx = (long long)arow * args.out_ld + c;
+        }
+        y.y *= csign;
+        st_cx(gout + idx, y);
+    }
+}
+
+} // namespace paco

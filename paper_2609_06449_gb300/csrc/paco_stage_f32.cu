@@ -1,0 +1,6 @@
+// Stage kernels for complex64 (FP32 arithmetic).
+#include "paco_stage_launch.cuh"
+
+namespace paco {
+const void *stage_kernel_fn_f32(int lgL) { return stage_kernel_fn<float>(lgL); }
+} // namespace paco

@@ -1,0 +1,6 @@
+// Stage kernels for complex128 (FP64 arithmetic).
+#include "paco_stage_launch.cuh"
+
+namespace paco {
+const void *stage_kernel_fn_f64(int lgL) { return stage_kernel_fn<double>(lgL); }
+} // namespace paco

@@ -1,4 +1,5 @@
-"""pytest configuration: the `gpu` marker and import paths.
+"""pytest configuration: the `gpu` marker, import paths, and an up-to-date
+build of the CUDA library and the C oracle before any test imports them.
 
 Tests marked ``gpu`` need a GB300 and the CUDA library built for sm_103a;
 everything else runs on the CPU (``-m "not gpu"``)."""
@@ -13,3 +14,6 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    import __graft_entry__
+
+    __graft_entry__.build()   # no-op when the builds are current

@@ -1,0 +1,75 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry
+point include/paco.h declares, computes the digit reversal of Sect. 3.2
+exactly like the oracle's digit-array reversal, and rejects illegal plans
+before touching a device."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "paco.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(paco_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_2609_06449_gb300 as paco
+    lib = ctypes.CDLL(paco.library_path)
+    names = _declared()
+    assert "paco_execute" in names and "paco_plan_create" in names
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in paco.h but not exported"
+
+
+@pytest.mark.parametrize("b", [2, 4, 8, 16])
+def test_digit_reverse_matches_oracle(b):
+    import paper_2609_06449_gb300 as paco
+    t = b.bit_length() - 1
+    for ell in range(1, 31 // t + 1):
+        n = b ** ell
+        us = np.arange(n) if n <= 4096 else np.random.default_rng(ell).integers(0, n, 4096)
+        for u in us:
+            assert paco.digit_reverse(int(u), b, ell) == oracle.digit_reverse(int(u), b, ell)
+
+
+def test_digit_reverse_rejects_bad_arguments():
+    import paper_2609_06449_gb300 as paco
+    with pytest.raises(paco.PacoError):
+        paco.digit_reverse(8, 2, 3)       # 8 has 4 binary digits
+    with pytest.raises(paco.PacoError):
+        paco.digit_reverse(1, 3, 2)       # b must be a power of two <= 16
+
+
+@pytest.mark.parametrize("N1,N2,b,p,msg", [
+    (256, 256, 3, 0, "radix"),
+    (96, 256, 2, 0, "N1"),
+    (256, 128, 4, 0, "N2"),            # 128 is not a power of 4
+    (256, 256, 2, 3, "p="),
+    (256, 256, 4, 2, "p="),            # 2 is not a power of 4
+    (16, 16, 2, 32, "p="),             # p does not divide N1
+    (2 ** 16, 16, 2, 0, "2^14"),       # factor not built
+])
+def test_plan_rejects_illegal_sizes(N1, N2, b, p, msg):
+    import paper_2609_06449_gb300 as paco
+    with pytest.raises(paco.PacoError) as ei:
+        paco.Plan(N1, N2, b, 1, paco.C64, p=p)
+    assert msg in str(ei.value)
+    assert ei.value.status in (1, 2)
+
+
+def test_plan_rejects_negative_batch_and_bad_dtype():
+    import paper_2609_06449_gb300 as paco
+    with pytest.raises(paco.PacoError):
+        paco.Plan(16, 16, 2, -1, paco.C64)
+    with pytest.raises(paco.PacoError):
+        paco.Plan(16, 16, 2, 1, 9)

@@ -1,0 +1,178 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Floating-point tolerance (relative L2 error per transform against the FP64
+oracle on the same rounded inputs): 5e-7*log2(N) for complex64 and
+1e-14*log2(N) for complex128.  Index work (where each value lands) is checked
+through the intermediates of Eq. (17) and Lemma 1 against the step-by-step
+simulator."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import paco_sim as ps
+from paco_inputs import gaussian, uniform
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2609_06449_gb300 as paco  # noqa: E402
+
+TOL = {paco.C64: 5e-7, paco.C128: 1e-14}
+NP = {paco.C64: np.complex64, paco.C128: np.complex128}
+TT = {paco.C64: torch.complex64, paco.C128: torch.complex128}
+
+
+def rel_l2(got, ref):
+    got = np.asarray(got, dtype=np.complex128).reshape(ref.shape)
+    num = np.linalg.norm(got - ref, axis=-1)
+    den = np.linalg.norm(ref, axis=-1)
+    return float(np.max(num / den))
+
+
+def run(plan, x_np, dir=-1):
+    x = torch.from_numpy(x_np).cuda()
+    out = torch.empty_like(x)
+    plan.execute(x, out, dir)
+    torch.cuda.synchronize()
+    plan.check()
+    return out.cpu().numpy()
+
+
+CASES = [  # (N1, N2, b, p)
+    (2, 2, 2, 2), (2, 8, 2, 2), (8, 2, 2, 2), (4, 4, 2, 2), (4, 4, 4, 4),
+    (16, 16, 2, 2), (16, 16, 4, 4), (16, 16, 16, 16), (32, 32, 2, 2),
+    (64, 16, 4, 4), (16, 64, 4, 4), (8, 64, 8, 8), (256, 256, 2, 4),
+    (128, 512, 2, 4), (512, 128, 2, 8), (1024, 1024, 4, 4), (4096, 64, 4, 16),
+    (64, 4096, 4, 4), (2048, 2048, 2, 16), (8192, 16, 2, 2), (16, 8192, 2, 2),
+    (4096, 4096, 16, 16), (16384, 16, 4, 4), (16, 16384, 4, 16),
+]
+
+
+@pytest.mark.parametrize("dtype", [paco.C64, paco.C128])
+@pytest.mark.parametrize("N1,N2,b,p", CASES)
+def test_end_to_end_vs_oracle(N1, N2, b, p, dtype):
+    N = N1 * N2
+    batch = 3 if N <= 2 ** 16 else 1
+    x = uniform(batch * N, N1 + 7 * N2, NP[dtype]).reshape(batch, N)
+    plan = paco.Plan(N1, N2, b, batch, dtype, p=p)
+    tol = TOL[dtype] * max(1.0, math.log2(N))
+    for d in (-1, 1):
+        got = run(plan, x, d)
+        ref = oracle.fft(x.astype(np.complex128), dir=d)
+        err = rel_l2(got, ref)
+        assert err <= tol, f"dir={d} rel_l2={err:.3e} tol={tol:.3e}"
+
+
+@pytest.mark.parametrize("dtype", [paco.C64, paco.C128])
+@pytest.mark.parametrize("N1,N2,b,p", [(16, 16, 2, 2), (64, 16, 4, 4), (16, 64, 4, 4),
+                                       (64, 64, 8, 8), (256, 16, 16, 16), (256, 256, 2, 4),
+                                       (64, 256, 4, 16)])
+def test_intermediates_vs_simulator(N1, N2, b, p, dtype):
+    """Stage-1 output is W = Z-hat (Eq. (17)) and Phase I alone is A-tilde
+    (Lemma 1) -- both compared with the step-by-step simulator, so every
+    value must sit at the position the paper's permutation assigns."""
+    N = N1 * N2
+    x = gaussian(N, 3, NP[dtype])
+    plan = paco.Plan(N1, N2, b, 1, dtype, p=p)
+    ref = ps.simulate(x.astype(np.complex128), N1, N2, b, p, phase1="lemma")
+    xt = torch.from_numpy(x).cuda()
+    W = torch.empty_like(xt)
+    plan.execute_stage1(xt, W)
+    At = torch.empty_like(xt)
+    plan.execute_phase1(xt, At)
+    torch.cuda.synchronize()
+    tol = TOL[dtype] * math.log2(N)
+    Wg = W.cpu().numpy().reshape(N2, N1)
+    assert np.linalg.norm(Wg - ref["W"]) / np.linalg.norm(ref["W"]) <= tol
+    Ag = At.cpu().numpy().reshape(N1, N2)
+    assert np.linalg.norm(Ag - ref["A_tilde"]) / np.linalg.norm(ref["A_tilde"]) <= tol
+    # stage 2 in place on W gives the transform
+    plan.execute_stage2(W, W)
+    torch.cuda.synchronize()
+    assert rel_l2(W.cpu().numpy(), ref["Y"].reshape(1, N)) <= tol
+
+
+def test_config_a_and_direct_dft_subcase():
+    """N = 2^16 as 256 x 256, b = 2, p = 4, U[-1,1) from seed 0, forward; and
+    the 2^10 sub-case against the long-double direct DFT."""
+    x = uniform(2 ** 16, 0, np.complex64)
+    plan = paco.Plan(256, 256, 2, 1, paco.C64, p=4)
+    got = run(plan, x.reshape(1, -1))
+    ref = oracle.fft(x.astype(np.complex128))
+    assert rel_l2(got, ref.reshape(1, -1)) <= 5e-7 * 16
+    x10 = uniform(2 ** 10, 0, np.complex64)
+    plan10 = paco.Plan(32, 32, 2, 1, paco.C64, p=2)
+    got10 = run(plan10, x10.reshape(1, -1))
+    ref10 = oracle.dft_direct(x10.astype(np.complex128))
+    assert rel_l2(got10, ref10.reshape(1, -1)) <= 5e-7 * 10
+
+
+def test_closed_forms_on_gpu():
+    """delta -> constant; single tone -> N delta; Parseval."""
+    N1 = N2 = 256
+    N = N1 * N2
+    plan = paco.Plan(N1, N2, 4, 1, paco.C64, p=4)
+    d = np.zeros((1, N), np.complex64); d[0, 0] = 1
+    assert np.allclose(run(plan, d), 1.0, atol=1e-6)
+    f = 12345
+    tone = np.exp(2j * np.pi * f * np.arange(N) / N).astype(np.complex64).reshape(1, N)
+    y = run(plan, tone)
+    want = np.zeros(N); want[f] = N
+    assert np.max(np.abs(y[0] - want)) <= 5e-7 * 16 * N
+    x = gaussian(N, 1, np.complex64).reshape(1, N)
+    y = run(plan, x)
+    e_y = np.sum(np.abs(y.astype(np.complex128)) ** 2)
+    e_x = np.sum(np.abs(x.astype(np.complex128)) ** 2)
+    assert abs(e_y - N * e_x) / (N * e_x) < 1e-5
+
+
+def test_edge_cases():
+    # batch 0 is a no-op
+    plan0 = paco.Plan(64, 64, 4, 0, paco.C64)
+    plan0.execute(0, 0, -1)
+    # aliasing and bad direction are errors
+    plan = paco.Plan(64, 64, 4, 1, paco.C64)
+    x = torch.zeros(64 * 64, dtype=torch.complex64, device="cuda")
+    with pytest.raises(paco.PacoError) as ei:
+        plan.execute(x, x, -1)
+    assert ei.value.status == 3
+    y = torch.empty_like(x)
+    with pytest.raises(paco.PacoError):
+        plan.execute(x, y, 0)
+    with pytest.raises(paco.PacoError):
+        plan.execute(x[1:], y, -1)   # misaligned (8-byte offset)
+    # the largest stage length built (2^14) in both factors: c64, b = 2
+    xs = uniform(2 ** 14 * 16, 2, np.complex64).reshape(1, -1)
+    planb = paco.Plan(2 ** 14, 16, 2, 1, paco.C64)
+    assert rel_l2(run(planb, xs), oracle.fft(xs.astype(np.complex128))) <= 5e-7 * 18
+
+
+def test_host_buffer_entry_point():
+    N1, N2 = 1024, 256
+    N = N1 * N2
+    x = uniform(2 * N, 4, np.complex64).reshape(2, N)
+    plan = paco.Plan(N1, N2, 4, 2, paco.C64)
+    h_in = torch.from_numpy(x).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty(h_in.shape, dtype=h_in.dtype, device="cuda")
+    d_out = torch.empty_like(d_in)
+    plan.execute_host(h_in, h_out, d_in, d_out, -1)
+    torch.cuda.synchronize()
+    assert rel_l2(h_out.numpy(), oracle.fft(x.astype(np.complex128))) <= 5e-7 * 18
+
+
+def test_torch_wrapper_and_stream():
+    N1, N2 = 256, 64
+    x = torch.from_numpy(gaussian(4 * N1 * N2, 8, np.complex64)).reshape(4, N1 * N2).cuda()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        y = paco.fft(x, N1, N2, 4)
+    s.synchronize()
+    ref = oracle.fft(x.cpu().numpy().astype(np.complex128))
+    assert rel_l2(y.cpu().numpy(), ref) <= 5e-7 * 14
