@@ -9,16 +9,22 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 
 #include "../../include/paco.h"
 #include "paco_common.cuh"
+#include "paco_panel.cuh"
 #include "paco_stage.cuh"
 
 namespace paco {
 const void *stage_kernel_fn_f32(int lgL);
 const void *stage_kernel_fn_f64(int lgL);
+const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
+const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
+const void *panel_kernel_fn();
+int panel_smem_bytes();
 } // namespace paco
 
 using namespace paco;
@@ -60,6 +66,8 @@ struct StageCfg {
     int smem = 0;     // dynamic shared memory, bytes
     int ntiles = 0;   // column tiles per transform
     const void *fn = nullptr;
+    int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
+    int P = 0;        // panel width (columns)
 };
 
 struct paco_plan {
@@ -73,6 +81,10 @@ struct paco_plan {
     void *twL1 = nullptr, *twL2 = nullptr, *twN_lo = nullptr, *twN_hi = nullptr;
     int twN_lo_bits = 0;
     int *d_status = nullptr;
+    void *scratch = nullptr;       // panel ring buffers (L2-sized, not N-sized)
+    unsigned *ctr = nullptr;       // panel pipeline counters
+    size_t ctr_words = 0;
+    int num_sms = 0;
 };
 
 static int ilog2_exact(int64_t v)
@@ -141,10 +153,22 @@ static void choose_tile(const paco_plan *pl, int lgL, int64_t C, int req_w, int 
     *lgK_out = lgK;
 }
 
+static const int kPanelWidth = 128;
+
 static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode,
                                  int req_w, int req_k)
 {
     sc->lgL = lgL;
+    if (pl->esize == 8 && lgL == 14 && (mode == 1 || mode == 2) && C >= kPanelWidth &&
+        req_w == 0 && req_k == 0) {
+        sc->panel = 1;
+        sc->P = kPanelWidth;
+        sc->fn = panel_kernel_fn();
+        sc->threads = panel::NT;
+        sc->smem = panel_smem_bytes();
+        PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sc->smem));
+        return PACO_OK;
+    }
     choose_tile(pl, lgL, C, req_w, req_k, &sc->lgW, &sc->lgK);
     if (sc->lgW < 0 || sc->lgK < 0 || sc->lgK > 3)
         return fail(PACO_ERR_INVALID_ARG, "tile width / cluster size must be powers of two, cluster <= 8");
@@ -156,7 +180,9 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
     const int EPT = L < 16 ? L : 16;
     const int64_t NE = (int64_t)A * (B / K) * W;     // elements per CTA
     sc->ntiles = (int)(C / W);
-    sc->fn = (pl->esize == 8) ? stage_kernel_fn_f32(lgL) : stage_kernel_fn_f64(lgL);
+    sc->fn = (pl->esize == 8) ? stage_kernel_fn_special_f32(lgL, sc->lgW, sc->lgK, mode)
+                              : stage_kernel_fn_special_f64(lgL, sc->lgW, sc->lgK, mode);
+    if (!sc->fn) sc->fn = (pl->esize == 8) ? stage_kernel_fn_f32(lgL) : stage_kernel_fn_f64(lgL);
     if (!sc->fn) return fail(PACO_ERR_UNSUPPORTED, "stage length 2^%d is not built (max 2^14)", lgL);
     if (B == 1) {
         sc->threads = W;
@@ -230,6 +256,24 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
         paco_plan_destroy(pl);
         return st;
     }
+    cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+    size_t scratch_elems = 0, words = 0;
+    for (int k = 0; k < 2; ++k) {
+        const StageCfg &sc = pl->st[k];
+        if (!sc.panel) continue;
+        const int64_t C = (k == 0) ? pl->N2 : pl->N1;
+        scratch_elems = std::max(scratch_elems, (size_t)panel::NBUF * ((size_t)1 << sc.lgL) * sc.P);
+        words = std::max(words, (size_t)(2 * pl->batch * (C / sc.P) + 1));
+    }
+    if (scratch_elems) {
+        cudaError_t ea = cudaMalloc(&pl->scratch, scratch_elems * pl->esize);
+        if (ea == cudaSuccess) ea = cudaMalloc((void **)&pl->ctr, words * sizeof(unsigned));
+        if (ea != cudaSuccess) {
+            paco_plan_destroy(pl);
+            return fail(PACO_ERR_NOMEM, "panel scratch: %s", cudaGetErrorString(ea));
+        }
+        pl->ctr_words = words;
+    }
     cudaError_t e = cudaMalloc(&pl->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -266,6 +310,8 @@ extern "C" void paco_plan_destroy(paco_plan_t *pl)
     cudaFree(pl->twN_lo);
     cudaFree(pl->twN_hi);
     cudaFree(pl->d_status);
+    cudaFree(pl->scratch);
+    cudaFree(pl->ctr);
     delete pl;
 }
 
@@ -294,9 +340,53 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
 // ---------------------------------------------------------------------------
 // execution
 // ---------------------------------------------------------------------------
+static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int mode,
+                                  const void *in, void *out, int dir, cudaStream_t stream)
+{
+    PanelArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.scratch = pl->scratch;
+    a.ctr = pl->ctr;
+    a.status = pl->d_status;
+    a.batch_stride = pl->N;
+    a.mode = mode;
+    a.P = sc.P;
+    a.rev_t = pl->t;
+    a.rev_bits = pl->m2 * pl->t;
+    a.conj = (dir == 1);
+    a.N_mask = (unsigned)(pl->N - 1);
+    a.twN_lo = pl->twN_lo;
+    a.twN_hi = pl->twN_hi;
+    a.twN_lo_bits = pl->twN_lo_bits;
+    a.spin_limit = 1u << 22;
+    if (mode == 1) {
+        a.C = (int)pl->N2;
+        a.out_ld = (int)pl->N1;
+        a.twL = pl->twL1;
+    } else {
+        a.C = (int)pl->N1;
+        a.out_ld = (int)pl->N1;
+        a.twL = pl->twL2;
+    }
+    a.panels_per_batch = a.C / sc.P;
+    a.npanels = (int)(pl->batch * a.panels_per_batch);
+    const size_t words = (size_t)(2 * a.npanels + 1);
+    PACO_CUDA_TRY(cudaMemsetAsync(pl->ctr, 0, words * sizeof(unsigned), stream));
+    const long long total = 2LL * a.npanels * ((long long)panel::L / panel::TILE) * sc.P;
+    long long grid = (long long)pl->num_sms * 2;
+    if (grid > total) grid = total;
+    void *params[] = {&a};
+    PACO_CUDA_TRY(cudaLaunchKernel(sc.fn, dim3((unsigned)grid), dim3(panel::NT), params,
+                                   (size_t)sc.smem, stream));
+    return PACO_OK;
+}
+
 static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int mode,
                                   const void *in, void *out, int dir, cudaStream_t stream)
 {
+    if (sc.panel) return launch_panel(pl, sc, mode, in, out, dir, stream);
     StageArgs a;
     memset(&a, 0, sizeof(a));
     a.in = in;

@@ -81,8 +81,11 @@ __host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int 
     return data + A + B + SL + SH + Ak * W + B * W;
 }
 
-template <typename R, int A, int B>
-__global__ void __launch_bounds__(512) paco_stage_kernel(const StageArgs args)
+// LGWC, LGKC, MC > 0 fix log2 W, log2 K and the mode at compile time (the
+// hot configurations); 0 takes them from args at run time.  MINB is the
+// minimum number of resident CTAs per SM requested from the compiler.
+template <typename R, int A, int B, int LGWC = -1, int LGKC = -1, int MC = 0, int MINB = 1>
+__global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs args)
 {
     using C = cx<R>;
     constexpr int L = A * B;
@@ -101,14 +104,15 @@ __global__ void __launch_bounds__(512) paco_stage_kernel(const StageArgs args)
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
 
-    const int lgW = args.lgW, lgK = args.lgK;
+    const int lgW = (LGWC >= 0) ? LGWC : args.lgW;
+    const int lgK = (LGKC >= 0) ? LGKC : args.lgK;
     const int W = 1 << lgW, K = 1 << lgK;
     const int Bk = B >> lgK, Ak = A >> lgK;
     const int S1 = Bk << lgW;                     // F1 sequences per CTA
     const int P2 = (B << lgW) + args.pad;         // F2 row stride
     const int P1 = (K == 1) ? P2 : S1;            // F1 row stride
     const int NT = blockDim.x;
-    const int mode = args.mode;
+    const int mode = MC ? MC : args.mode;
 
     C *sm = reinterpret_cast<C *>(smem_raw);
     const int data_elems = (A * P1 > Ak * P2) ? A * P1 : Ak * P2;

@@ -3,4 +3,8 @@
 
 namespace paco {
 const void *stage_kernel_fn_f32(int lgL) { return stage_kernel_fn<float>(lgL); }
+const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode)
+{
+    return stage_kernel_fn_special<float>(lgL, lgW, lgK, mode);
+}
 } // namespace paco

@@ -40,4 +40,18 @@ const void *stage_kernel_fn(int lgL)
     }
 }
 
+// Specialised kernels for the hot configurations: (A, B, log2 W, log2 K,
+// mode).  Returns nullptr when there is none.
+template <typename R>
+const void *stage_kernel_fn_special(int lgL, int lgW, int lgK, int mode)
+{
+    if constexpr (sizeof(R) == 4) {
+        if (lgL == 14 && lgW == 2 && lgK == 3) {
+            if (mode == 1) return reinterpret_cast<const void *>(&paco_stage_kernel<R, 128, 128, 2, 3, 1, 2>);
+            if (mode == 2) return reinterpret_cast<const void *>(&paco_stage_kernel<R, 128, 128, 2, 3, 2, 2>);
+        }
+    }
+    return nullptr;
+}
+
 } // namespace paco

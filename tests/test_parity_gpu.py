@@ -51,6 +51,7 @@ CASES = [  # (N1, N2, b, p)
     (128, 512, 2, 4), (512, 128, 2, 8), (1024, 1024, 4, 4), (4096, 64, 4, 16),
     (64, 4096, 4, 4), (2048, 2048, 2, 16), (8192, 16, 2, 2), (16, 8192, 2, 2),
     (4096, 4096, 16, 16), (16384, 16, 4, 4), (16, 16384, 4, 16),
+    (16384, 128, 2, 2), (128, 16384, 2, 4), (16384, 256, 4, 16), (256, 16384, 4, 4),
 ]
 
 
@@ -72,7 +73,7 @@ def test_end_to_end_vs_oracle(N1, N2, b, p, dtype):
 @pytest.mark.parametrize("dtype", [paco.C64, paco.C128])
 @pytest.mark.parametrize("N1,N2,b,p", [(16, 16, 2, 2), (64, 16, 4, 4), (16, 64, 4, 4),
                                        (64, 64, 8, 8), (256, 16, 16, 16), (256, 256, 2, 4),
-                                       (64, 256, 4, 16)])
+                                       (64, 256, 4, 16), (16384, 256, 4, 4), (256, 16384, 4, 4)])
 def test_intermediates_vs_simulator(N1, N2, b, p, dtype):
     """Stage-1 output is W = Z-hat (Eq. (17)) and Phase I alone is A-tilde
     (Lemma 1) -- both compared with the step-by-step simulator, so every
@@ -176,3 +177,31 @@ def test_torch_wrapper_and_stream():
     s.synchronize()
     ref = oracle.fft(x.cpu().numpy().astype(np.complex128))
     assert rel_l2(y.cpu().numpy(), ref) <= 5e-7 * 14
+
+
+def test_full_size_bench_configuration():
+    """N = 2^28 c64 as 2^14 x 2^14, b = 4, p = 64 -- the configuration bench.py
+    times -- on sampled outputs, each against the DFT definition evaluated by
+    the oracle at that index, plus Parseval over the whole vector."""
+    N1 = N2 = 2 ** 14
+    N = N1 * N2
+    x = uniform(N, 0, np.complex64)
+    plan = paco.Plan(N1, N2, 4, 1, paco.C64, p=64)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    plan.execute(xd, yd, -1)
+    torch.cuda.synchronize()
+    plan.check()
+    rng = np.random.default_rng(1)
+    ks = np.concatenate([[0, 1, N1 - 1, N1, N // 2, N - 1, 12345 * N1 + 77],
+                         rng.integers(0, N, 9)])
+    ref = oracle.dft_at(x.astype(np.complex128), ks, -1)
+    got = yd[torch.from_numpy(ks).cuda()].cpu().numpy().astype(np.complex128)
+    rms = np.sqrt(N * np.mean(np.abs(x.astype(np.complex128)) ** 2))   # rms |y_k|
+    err = np.max(np.abs(got - ref)) / rms
+    assert err <= 5e-7 * 28, f"sampled max error / rms = {err:.3e}"
+    ey = torch.sum(torch.abs(yd.to(torch.complex128)) ** 2).item()
+    ex = float(np.sum(np.abs(x.astype(np.complex128)) ** 2))
+    assert abs(ey - N * ex) / (N * ex) < 1e-5
+    del xd, yd
+    torch.cuda.empty_cache()
