@@ -26,10 +26,8 @@ const void *stage_kernel_fn_f32(int lgL);
 const void *stage_kernel_fn_f64(int lgL);
 const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
-const void *panel_kernel_fn(int prefetch);
+const void *panel_kernel_fn();
 int panel_smem_bytes();
-const void *panel_tma_kernel_fn();
-int panel_tma_smem_bytes();
 } // namespace paco
 
 using namespace paco;
@@ -73,7 +71,6 @@ struct StageCfg {
     const void *fn = nullptr;
     int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
     int P = 0;        // panel width (columns)
-    int prefetch = 0; // panel kernel variant: 1 = one CTA/SM with register prefetch
 };
 
 struct paco_plan {
@@ -169,18 +166,9 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         req_w == 0 && req_k == 0) {
         sc->panel = 1;
         sc->P = kPanelWidth;
-        sc->prefetch = getenv("PACO_PANEL_PREFETCH") ? atoi(getenv("PACO_PANEL_PREFETCH")) : 2;
-        if (sc->prefetch == 2) {
-            sc->fn = panel_tma_kernel_fn();
-            sc->smem = panel_tma_smem_bytes();
-            sc->threads = panel::NT + 32;                    // 16 consumer warps + 1 producer
-        } else {
-            sc->fn = panel_kernel_fn(sc->prefetch);
-        }
-        if (sc->prefetch != 2) {
-            sc->threads = panel::NT;
-            sc->smem = panel_smem_bytes();
-        }
+        sc->fn = panel_kernel_fn();
+        sc->smem = panel_smem_bytes();
+        sc->threads = panel::NT + 32;                        // 16 consumer warps + 1 producer
         PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sc->smem));
         return PACO_OK;
     }
@@ -397,7 +385,12 @@ static bool panel_maps(const paco_plan *pl, const StageCfg &sc, int mode, const 
         const cuuint64_t dims[4] = {(cuuint64_t)pl->N2, 128, 128, (cuuint64_t)pl->batch};
         const cuuint64_t str[3] = {(cuuint64_t)pl->N2 * E, (cuuint64_t)pl->N2 * 128 * E, (cuuint64_t)pl->N * E};
         const cuuint32_t box[4] = {16, 4, 128, 1};
-        return encode_map(&a->map_in, in, 4, dims, str, box, true);
+        if (!encode_map(&a->map_in, in, 4, dims, str, box, true)) return false;
+        // scratch [c][j_lo >> 3][k_lo][j_lo & 7] as (j_lo & 7, k_lo, j_lo >> 3, c)
+        const cuuint64_t sdims[4] = {8, 128, 16, (cuuint64_t)sc.P * panel::NBUF};
+        const cuuint64_t sstr[3] = {8 * E, 128 * 8 * E, 16 * 128 * 8 * E};
+        const cuuint32_t sbox[4] = {8, 64, 16, 1};
+        return encode_map(&a->map_scr, pl->scratch, 4, sdims, sstr, sbox, false);
     }
     const int bits = pl->m2 * pl->t;                 // log2 N2 = 14
     unsigned vmask = 0;
@@ -466,14 +459,14 @@ static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int m
         a.twL = pl->twL2;
     }
     a.panels_per_batch = a.C / sc.P;
-    if (sc.prefetch == 2 && !getenv("PACO_PANEL_NO_TENSOR")) a.use_tensor = panel_maps(pl, sc, mode, in, &a) ? 1 : 0;
+    a.use_tensor = panel_maps(pl, sc, mode, in, &a) ? 1 : 0;
     a.lgP = ilog2_exact(sc.P);
     a.lgPpb = ilog2_exact(a.panels_per_batch);
     a.npanels = (int)(pl->batch * a.panels_per_batch);
     const size_t words = (size_t)(2 * a.npanels + 1);
     PACO_CUDA_TRY(cudaMemsetAsync(pl->ctr, 0, words * sizeof(unsigned), stream));
     const long long total = 2LL * a.npanels * ((long long)panel::L / panel::TILE) * sc.P;
-    long long grid = (long long)pl->num_sms * (sc.prefetch ? 1 : 2);   // TMA (2) and prefetch (1): one CTA per SM
+    long long grid = (long long)pl->num_sms;                 // one persistent CTA per SM
     if (grid > total) grid = total;
     void *params[] = {&a};
     PACO_CUDA_TRY(cudaLaunchKernel(sc.fn, dim3((unsigned)grid), dim3((unsigned)sc.threads), params,
