@@ -208,6 +208,33 @@ int64_t paco_digit_reverse(int64_t u, int b, int ell);
 /* paco_version -- library version string. */
 const char *paco_version(void);
 
+/* Largest batch that paco_execute_noalloc accepts. */
+#define PACO_NOALLOC_MAX_BATCH 16
+
+/*
+ * paco_execute_noalloc -- the complex64 transform of paco_execute for
+ * N1 = N2 = 2^14 (N = 2^28, b = 2 or 4), for callers that cannot allocate
+ * device memory: code running while a CUDA graph is captured, inside a
+ * framework whose pool owns the device memory, or anywhere the allocator must
+ * not be touched after start-up.  The paper has no counterpart; this is a
+ * deployment form of the same kernels.  No plan: everything it needs (panel
+ * buffers, pipeline counters, status word, twiddle tables; about 24.4 MiB)
+ * lives in device arrays that the library reserves on every GPU that loads it,
+ * until the process exits.  The call allocates and frees nothing.
+ *   in, out  device buffers of batch * 2^28 complex64 values, 16-byte aligned,
+ *            not overlapping (layout as paco_execute); 0 <= batch <=
+ *            PACO_NOALLOC_MAX_BATCH, larger batches return
+ *            PACO_ERR_INVALID_ARG; b other than 2 or 4 too.
+ * The first call on a device takes the arrays' device addresses and fills the
+ * twiddle tables (synchronously); make it before any stream capture.  Later
+ * calls only enqueue work on `stream`.  All calls on one device share the
+ * arrays and each leaves its intermediates there: calls whose work overlaps on
+ * the GPU race and must be ordered by the caller.  Errors are reported as for
+ * the other entry points (paco_last_error()).
+ */
+paco_status_t paco_execute_noalloc(const void *in, void *out, int b, int64_t batch, int dir,
+                                   paco_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -106,6 +106,8 @@ def _load():
     L.paco_digit_reverse.restype = i64
     L.paco_version.argtypes = []
     L.paco_version.restype = ctypes.c_char_p
+    L.paco_execute_noalloc.argtypes = [vp, vp, i32, i64, i32, vp]
+    L.paco_execute_noalloc.restype = i32
     return L
 
 
@@ -115,6 +117,12 @@ lib = _load()
 def _check(status: int) -> None:
     if status != 0:
         raise PacoError(status, lib.paco_last_error().decode())
+
+
+def execute_noalloc(x, out, b: int, batch: int, dir: int = -1, stream=None) -> None:
+    """paco_execute_noalloc: the N1 = N2 = 2^14 complex64 transform without
+    any allocation (the library's reserved device arrays); see paco.h."""
+    _check(lib.paco_execute_noalloc(_ptr(x), _ptr(out), int(b), int(batch), int(dir), _stream(stream)))
 
 
 def digit_reverse(u: int, b: int, ell: int) -> int:

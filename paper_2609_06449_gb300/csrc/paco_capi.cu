@@ -56,6 +56,10 @@ static paco_status_t fail(paco_status_t st, const char *fmt, ...)
     } while (0)
 
 extern "C" const char *paco_last_error(void) { return g_last_error.c_str(); }
+
+namespace paco {
+void set_last_error(const char *msg) { g_last_error = msg; }
+} // namespace paco
 extern "C" const char *paco_version(void) { return "paco-gb300 0.1"; }
 
 // ---------------------------------------------------------------------------

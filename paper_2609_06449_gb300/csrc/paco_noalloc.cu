@@ -1,0 +1,268 @@
+// paco_noalloc.cu -- paco_execute_noalloc: the complex64 transform of
+// N1 = N2 = 2^14 run only from memory the library reserves when it is loaded.
+//
+// Some callers cannot allocate device memory: code that runs while a CUDA
+// graph is being captured, inside a framework whose memory pool owns every
+// byte of the device, or in a context that must not touch the allocator after
+// start-up.  This entry point serves them: the panel buffers the length-2^14
+// stages stream through, the pipeline counters, the status word and the
+// twiddle tables are file-scope __device__ arrays, so a call allocates and
+// frees nothing.  Every GPU that loads the library holds these arrays (about
+// 24.4 MiB) until the process exits.
+//
+// In host code the names of these arrays are host-side stand-ins, not device
+// addresses; the device addresses come from cudaGetSymbolAddress, taken once
+// per device (with that device current) by the first call on the device, which
+// also fills the twiddle tables.  That first call should therefore come before
+// any stream capture.  All calls on a device share the arrays and each call
+// leaves them holding its own intermediates: the counters are cleared on the
+// stream at the start of every stage; calls whose work overlaps on the GPU
+// race on the shared buffers and must be ordered by the caller.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "../../include/paco.h"
+#include "paco_common.cuh"
+#include "paco_panel.cuh"
+
+namespace paco {
+const void *panel_kernel_fn();
+int panel_smem_bytes();
+void set_last_error(const char *msg);          // message for paco_last_error()
+} // namespace paco
+
+using namespace paco;
+
+namespace {
+
+constexpr int kLg = 14;                                  // N1 = N2 = 2^14
+constexpr long long kL = 1LL << kLg;
+constexpr long long kN = kL * kL;
+constexpr int kP = 64;                                   // panel width (columns)
+constexpr long long kPanelsPerBatch = kL / kP;           // 256
+constexpr long long kScratchElems = (long long)panel::NBUF * kL * kP;   // 3 * 2^20
+constexpr int kCtrWords = (int)(2 * PACO_NOALLOC_MAX_BATCH * kPanelsPerBatch + 1);
+
+__device__ __align__(256) float2 g_scratch[kScratchElems];   // 24 MiB panel ring
+__device__ __align__(256) unsigned g_ctr[kCtrWords];         // queue + per-panel counters
+__device__ __align__(256) int g_status;                      // PACO_ERR_TIMEOUT from bounded waits
+__device__ __align__(256) float2 g_twL[kL];                  // w_{2^14}^{-r}
+__device__ __align__(256) float2 g_twN_lo[kL];               // w_{2^28}^{-r}, r < 2^14
+__device__ __align__(256) float2 g_twN_hi[kL];               // w_{2^28}^{-r 2^14}
+
+// FP64 twiddles, rounded to FP32: w_M^{-e} = (cos 2 pi e / M, -sin 2 pi e / M).
+__global__ void noalloc_tables_kernel(float2 *twL, float2 *lo, float2 *hi)
+{
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= kL) return;
+    double s, c;
+    sincospi(2.0 * (double)r / (double)kL, &s, &c);
+    twL[r] = make_float2((float)c, (float)-s);
+    sincospi(2.0 * (double)r / (double)kN, &s, &c);
+    lo[r] = make_float2((float)c, (float)-s);
+    sincospi(2.0 * (double)(r * kL) / (double)kN, &s, &c);
+    hi[r] = make_float2((float)c, (float)-s);
+}
+
+struct DeviceState {
+    bool ready = false;
+    float2 *scratch = nullptr, *twL = nullptr, *lo = nullptr, *hi = nullptr;
+    unsigned *ctr = nullptr;
+    int *status = nullptr;
+    int num_sms = 0;
+};
+
+constexpr int kMaxDevices = 64;
+DeviceState g_state[kMaxDevices];
+std::mutex g_mutex;
+
+paco_status_t fail(paco_status_t st, const char *msg)
+{
+    set_last_error(msg);
+    return st;
+}
+
+// Set-up for the current device, once: symbol addresses, tables, attributes.
+paco_status_t setup(int dev, DeviceState **out)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    DeviceState &s = g_state[dev];
+    if (!s.ready) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return fail(PACO_ERR_CUDA, "cudaGetSymbolAddress(scratch) failed");
+        s.scratch = static_cast<float2 *>(p);
+        if (cudaGetSymbolAddress(&p, g_ctr) != cudaSuccess) return fail(PACO_ERR_CUDA, "cudaGetSymbolAddress(counters) failed");
+        s.ctr = static_cast<unsigned *>(p);
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return fail(PACO_ERR_CUDA, "cudaGetSymbolAddress(status) failed");
+        s.status = static_cast<int *>(p);
+        if (cudaGetSymbolAddress(&p, g_twL) != cudaSuccess) return fail(PACO_ERR_CUDA, "cudaGetSymbolAddress(twL) failed");
+        s.twL = static_cast<float2 *>(p);
+        if (cudaGetSymbolAddress(&p, g_twN_lo) != cudaSuccess) return fail(PACO_ERR_CUDA, "cudaGetSymbolAddress(twN_lo) failed");
+        s.lo = static_cast<float2 *>(p);
+        if (cudaGetSymbolAddress(&p, g_twN_hi) != cudaSuccess) return fail(PACO_ERR_CUDA, "cudaGetSymbolAddress(twN_hi) failed");
+        s.hi = static_cast<float2 *>(p);
+        if (cudaFuncSetAttribute(panel_kernel_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 panel_smem_bytes()) != cudaSuccess)
+            return fail(PACO_ERR_CUDA, "cudaFuncSetAttribute failed");
+        if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return fail(PACO_ERR_CUDA, "cudaDeviceGetAttribute failed");
+        noalloc_tables_kernel<<<(unsigned)(kL / 256), 256>>>(s.twL, s.lo, s.hi);
+        if (cudaGetLastError() != cudaSuccess || cudaMemset(s.status, 0, sizeof(int)) != cudaSuccess ||
+            cudaDeviceSynchronize() != cudaSuccess)
+            return fail(PACO_ERR_CUDA, "table set-up failed");
+        s.ready = true;
+    }
+    *out = &s;
+    return PACO_OK;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!tried) {
+        tried = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    return fn;
+}
+
+bool encode(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims, const cuuint64_t *str,
+            const cuuint32_t *box, bool promote)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) return false;
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<void *>(base), dims, str, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Arguments of one stage (mode 1: in -> out; mode 2: out in place).
+bool stage_args(const DeviceState &s, int mode, int b, int t, long long batch, const void *in, void *out,
+                int dir, PanelArgs *a)
+{
+    memset(a, 0, sizeof(*a));
+    const int E = 8;
+    a->in = in;
+    a->out = out;
+    a->scratch = s.scratch;
+    a->ctr = s.ctr;
+    a->status = s.status;
+    a->batch_stride = kN;
+    a->C = (int)kL;
+    a->out_ld = (int)kL;
+    a->P = kP;
+    a->lgP = 6;
+    a->panels_per_batch = (int)kPanelsPerBatch;
+    a->lgPpb = 8;
+    a->npanels = (int)(batch * kPanelsPerBatch);
+    a->mode = mode;
+    a->rev_t = t;
+    a->rev_bits = kLg;
+    a->twL = s.twL;
+    a->twN_lo = s.lo;
+    a->twN_hi = s.hi;
+    a->twN_lo_bits = kLg;
+    a->N_mask = (unsigned)(kN - 1);
+    a->conj = (dir == 1);
+    a->spin_limit = 1u << 22;
+    if (mode == 1) {
+        const cuuint64_t dims[4] = {(cuuint64_t)kL, 128, 128, (cuuint64_t)batch};
+        const cuuint64_t str[3] = {(cuuint64_t)kL * E, (cuuint64_t)kL * 128 * E, (cuuint64_t)kN * E};
+        const cuuint32_t box[4] = {16, 4, 128, 1};
+        const cuuint64_t sdims[4] = {8, 128, 16, (cuuint64_t)kP * panel::NBUF};
+        const cuuint64_t sstr[3] = {8 * E, 128 * 8 * E, 16 * 128 * 8 * E};
+        const cuuint32_t sbox[4] = {8, 64, 16, 1};
+        a->use_tensor = encode(&a->map_in, in, 4, dims, str, box, true) &&
+                        encode(&a->map_scr, s.scratch, 4, sdims, sstr, sbox, false);
+        return true;
+    }
+    // stage 2: rows pi(j_lo + 128 j_hi) of W as runs of spanned / fixed bits
+    const int m2 = kLg / t;
+    unsigned vmask = 0;
+    for (int jh = 0; jh < 128; ++jh) vmask |= (unsigned)paco_digit_reverse((int64_t)jh << 7, b, m2);
+    int starts[8], fixed[8], nr = 0;
+    for (int bit = 0; bit < kLg; ++bit) {
+        const int f = !((vmask >> bit) & 1u);
+        if (nr == 0 || fixed[nr - 1] != f) {
+            if (nr == 8) return false;
+            starts[nr] = bit;
+            fixed[nr] = f;
+            ++nr;
+        }
+    }
+    if (nr > 4 || !fixed[nr - 1]) return false;
+    cuuint64_t dims[5], str[4];
+    cuuint32_t box[5];
+    dims[0] = (cuuint64_t)kL;
+    box[0] = 64;
+    for (int k = 0; k < nr; ++k) {
+        const int en = (k + 1 < nr) ? starts[k + 1] : kLg;
+        const cuuint64_t size = 1ull << (en - starts[k]);
+        dims[k + 1] = (k + 1 == nr) ? size * (cuuint64_t)batch : size;
+        str[k] = ((cuuint64_t)kL * E) << starts[k];
+        box[k + 1] = fixed[k] ? 1u : (cuuint32_t)size;
+        a->map_run_start[k] = starts[k];
+        a->map_run_fixed[k] = fixed[k];
+    }
+    a->map_rank = nr + 1;
+    a->vmask = vmask;
+    const cuuint64_t sdims[2] = {(cuuint64_t)kP, (cuuint64_t)panel::NBUF * 128 * 128};
+    const cuuint64_t sstr[1] = {(cuuint64_t)kP * E};
+    const cuuint32_t sbox[2] = {64, 128};
+    a->use_tensor = encode(&a->map_in, out, nr + 1, dims, str, box, true) &&
+                    encode(&a->map_scr, s.scratch, 2, sdims, sstr, sbox, false);
+    return true;
+}
+
+} // namespace
+
+extern "C" paco_status_t paco_execute_noalloc(const void *in, void *out, int b, int64_t batch, int dir,
+                                              paco_stream_t stream)
+{
+    if (b != 2 && b != 4) return fail(PACO_ERR_INVALID_ARG, "paco_execute_noalloc: b must be 2 or 4 (N1 = N2 = 2^14)");
+    if (batch < 0 || batch > PACO_NOALLOC_MAX_BATCH)
+        return fail(PACO_ERR_INVALID_ARG, "paco_execute_noalloc: batch must be in [0, PACO_NOALLOC_MAX_BATCH]");
+    if (dir != -1 && dir != 1) return fail(PACO_ERR_INVALID_ARG, "paco_execute_noalloc: dir must be -1 or +1");
+    if (batch == 0) return PACO_OK;
+    if (!in || !out) return fail(PACO_ERR_INVALID_ARG, "paco_execute_noalloc: NULL buffer");
+    if (((uintptr_t)in | (uintptr_t)out) & 15u)
+        return fail(PACO_ERR_INVALID_ARG, "paco_execute_noalloc: buffers must be 16-byte aligned");
+    const size_t bytes = (size_t)batch * (size_t)kN * 8;
+    const char *x = (const char *)in, *y = (const char *)out;
+    if (x < y + bytes && y < x + bytes) return fail(PACO_ERR_ALIASING, "paco_execute_noalloc: input and output overlap");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(PACO_ERR_CUDA, "paco_execute_noalloc: no current device");
+    DeviceState *s = nullptr;
+    paco_status_t st = setup(dev, &s);
+    if (st != PACO_OK) return st;
+    const int t = (b == 2) ? 1 : 2;
+    cudaStream_t cs = (cudaStream_t)stream;
+    const long long tiles = 2LL * batch * kPanelsPerBatch * (2 * kP);
+    const unsigned grid = (unsigned)(s->num_sms < tiles ? s->num_sms : tiles);
+    for (int mode = 1; mode <= 2; ++mode) {
+        PanelArgs a;
+        if (!stage_args(*s, mode, b, t, batch, mode == 1 ? in : out, out, dir, &a))
+            return fail(PACO_ERR_UNSUPPORTED, "paco_execute_noalloc: tensor layout not supported");
+        const size_t words = (size_t)(2 * a.npanels + 1);
+        if (cudaMemsetAsync(s->ctr, 0, words * sizeof(unsigned), cs) != cudaSuccess)
+            return fail(PACO_ERR_CUDA, "paco_execute_noalloc: counter reset failed");
+        void *params[] = {&a};
+        if (cudaLaunchKernel(panel_kernel_fn(), dim3(grid), dim3(panel::NT + 32), params,
+                             (size_t)panel_smem_bytes(), cs) != cudaSuccess)
+            return fail(PACO_ERR_CUDA, "paco_execute_noalloc: launch failed");
+    }
+    return PACO_OK;
+}
