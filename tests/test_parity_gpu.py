@@ -205,3 +205,24 @@ def test_full_size_bench_configuration():
     assert abs(ey - N * ex) / (N * ex) < 1e-5
     del xd, yd
     torch.cuda.empty_cache()
+
+
+def test_full_size_complex128():
+    """complex128 N = 2^27 as 2^13 x 2^14, b = 2, p = 128 (the FP64
+    configuration of the large-scale workload), forward and conjugate, against
+    the oracle's full FP64 FFT; tolerance 1e-14 * log2 N."""
+    N1, N2 = 2 ** 13, 2 ** 14
+    N = N1 * N2
+    x = uniform(N, 0, np.complex128)
+    plan = paco.Plan(N1, N2, 2, 1, paco.C128, p=128)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    for d in (-1, 1):
+        plan.execute(xd, yd, d)
+        torch.cuda.synchronize()
+        plan.check()
+        ref = oracle.fft(x, dir=d, threads=0)
+        err = np.linalg.norm(yd.cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= 1e-14 * 27, f"dir={d} rel_l2={err:.3e}"
+    del xd, yd
+    torch.cuda.empty_cache()
