@@ -185,6 +185,50 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+class Ranks:
+    """The rank context of a bench run: one process per GPU under torchrun,
+    a single process otherwise.  `barrier`, `max_over_ranks` and
+    `job_value` are the only cross-rank operations (no data-path
+    collective: every rank runs an independent replica)."""
+
+    def __init__(self, backend: str | None = None, device=None):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        self.device = device
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist_mod
+            if not dist_mod.is_initialized():
+                if backend == "nccl":
+                    dist_mod.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+                else:
+                    dist_mod.init_process_group(backend or "gloo")
+            self.dist = dist_mod
+
+    def barrier(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max_over_ranks(self, v: float) -> float:
+        if self.dist is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def job_value(self, units_per_rank: float, seconds_per_step: float) -> float:
+        """Whole-job throughput: the units every rank processed in one step
+        over the slowest rank's step time."""
+        return units_per_rank * self.world / self.max_over_ranks(seconds_per_step)
+
+    def close(self) -> None:
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
 def workload_config(args):
     N1, N2 = 1 << args.lg1, 1 << args.lg2
     return {
@@ -234,8 +278,7 @@ def measured_peak_hbm():
 def main():
     args = parse_args()
     rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", str(args.gpus if args.gpus == 1 else 1)))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
 
     if args.impl == "reference":
         run_reference(args, rank, world)
@@ -247,23 +290,10 @@ def main():
     import paper_2609_06449_gb300 as paco
     from paco_inputs import uniform
 
+    local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist_mod
-        dist_mod.init_process_group("nccl", device_id=torch.device("cuda", local))
-        dist = dist_mod
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks("nccl", device="cuda")
+    barrier, max_over_ranks = ranks.barrier, ranks.max_over_ranks
 
     N1, N2 = 1 << args.lg1, 1 << args.lg2
     N = N1 * N2
@@ -307,10 +337,9 @@ def main():
     total_ms = ev[0][0].elapsed_time(ev[K - 1][2])
     s1 = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
     s2 = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
-    total_ms = max_over_ranks(total_ms)
-    ms_step = total_ms / K
     flop = 5.0 * N * lgN
-    value = flop * world / (ms_step * 1e-3) / 1e9
+    value = ranks.job_value(flop / 1e9, total_ms / K * 1e-3)
+    ms_step = max_over_ranks(total_ms) / K
     hbm_eff = 4.0 * N * esize * world / (ms_step * 1e-3) / 1e9
 
     avg1, avg2 = statistics.mean(s1), statistics.mean(s2)
@@ -373,8 +402,7 @@ def main():
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": 2 * K, "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 if __name__ == "__main__":
