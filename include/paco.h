@@ -208,6 +208,49 @@ int64_t paco_digit_reverse(int64_t u, int b, int ell);
 /* paco_version -- library version string. */
 const char *paco_version(void);
 
+/*
+ * Uneven batches.  The paper transforms one length at a time; its
+ * scheduler splits the transform and the batch dimensions with the same
+ * recursion (Sect. 4.1, batch field of the digit split), which is what a
+ * batch of many lengths needs.  This library runs such a batch as one
+ * persistent launch over a queue of equal-sized work items (the method per
+ * transform is unchanged: Phase I, fused twiddle + digit reversal, Phase III).
+ *
+ * paco_plan_create_batched -- plan for `count` complex64 transforms whose
+ * lengths are lengths[0..count) (each a power of two, 2^4 .. 2^20; the
+ * factorisation N = N1*N2 and the radix b are chosen per length).  Buffers
+ * passed to paco_execute / paco_execute_host hold the transforms back to
+ * back in the given order (transform i starts at element
+ * sum_{j<i} lengths[j]); each is computed as by a single-length plan (natural
+ * order in and out).  The default constructor autotunes: it times candidate
+ * configurations on plan-owned scratch buffers (allocated and freed inside
+ * the call, up to 2 x 256 MiB) and keeps the fastest.  Returns
+ * PACO_ERR_UNSUPPORTED for other dtypes or lengths, PACO_ERR_INVALID_ARG for
+ * a NULL list with count > 0.  Execution of such a plan is one
+ * cudaMemsetAsync of its counters and one kernel launch on `stream`, so it can
+ * be captured in a CUDA graph.  paco_execute_stage1/2, _phase1 and
+ * paco_permute return PACO_ERR_UNSUPPORTED for it; paco_plan_info reports
+ * N = the total length and batch = count.
+ */
+typedef struct {
+    int autotune;     /* 1: time candidates at plan creation (default constructor) */
+    int b;            /* 0: per length; else the radix for every length it fits */
+    int ctas_per_sm;  /* 1 or 2 resident CTAs per SM (autotuned when autotune=1) */
+    int lag;          /* Phase III lag after Phase I, in grids of work items (0: 2) */
+} paco_batched_opts_t;
+
+paco_status_t paco_plan_create_batched(paco_plan_t **out, const int64_t *lengths, int64_t count,
+                                       paco_dtype_t dtype);
+paco_status_t paco_plan_create_batched_ex(paco_plan_t **out, const int64_t *lengths, int64_t count,
+                                          paco_dtype_t dtype, const paco_batched_opts_t *opts);
+
+/* paco_plan_batched_config -- the configuration an uneven-batch plan uses
+ * for one of its lengths (radix b, first factor N1) and overall (CTAs per SM,
+ * Phase III lag).  Any output pointer may be NULL.  PACO_ERR_INVALID_ARG if
+ * the plan is not an uneven batch or does not hold that length. */
+paco_status_t paco_plan_batched_config(const paco_plan_t *plan, int64_t length, int *b, int *N1,
+                                       int *ctas_per_sm, int *lag);
+
 /* Largest batch that paco_execute_noalloc accepts. */
 #define PACO_NOALLOC_MAX_BATCH 16
 

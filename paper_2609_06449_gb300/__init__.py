@@ -22,6 +22,7 @@ import os
 __all__ = [
     "PacoError",
     "Plan",
+    "BatchedPlan",
     "lib",
     "library_path",
     "fft",
@@ -76,6 +77,11 @@ class PlanInfo(ctypes.Structure):
     ]
 
 
+class BatchedOpts(ctypes.Structure):
+    _fields_ = [("autotune", ctypes.c_int), ("b", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("lag", ctypes.c_int)]
+
+
 def _load():
     if not os.path.exists(library_path):
         raise ImportError(
@@ -106,6 +112,14 @@ def _load():
     L.paco_digit_reverse.restype = i64
     L.paco_version.argtypes = []
     L.paco_version.restype = ctypes.c_char_p
+    L.paco_plan_create_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i32]
+    L.paco_plan_create_batched.restype = i32
+    L.paco_plan_create_batched_ex.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i32,
+                                              ctypes.POINTER(BatchedOpts)]
+    L.paco_plan_create_batched_ex.restype = i32
+    pi = ctypes.POINTER(i32)
+    L.paco_plan_batched_config.argtypes = [vp, i64, pi, pi, pi, pi]
+    L.paco_plan_batched_config.restype = i32
     L.paco_execute_noalloc.argtypes = [vp, vp, i32, i64, i32, vp]
     L.paco_execute_noalloc.restype = i32
     return L
@@ -211,6 +225,37 @@ class Plan:
 
     def check(self) -> None:
         _check(lib.paco_plan_check(self._h))
+
+
+class BatchedPlan(Plan):
+    """An uneven batch (``paco_plan_create_batched``): ``lengths`` complex64
+    transforms stored back to back in the given order.  ``autotune=True`` is
+    the default constructor; otherwise ``b``, ``ctas_per_sm`` and ``lag`` fix
+    the configuration.  ``execute``/``execute_host`` as for ``Plan``."""
+
+    def __init__(self, lengths, autotune: bool = True, b: int = 0, ctas_per_sm: int = 1,
+                 lag: int = 0):
+        n = len(lengths)
+        arr = (ctypes.c_int64 * max(1, n))(*[int(v) for v in lengths])
+        h = ctypes.c_void_p()
+        if autotune and not b:
+            _check(lib.paco_plan_create_batched(ctypes.byref(h), arr, n, C64))
+        else:
+            o = BatchedOpts(1 if autotune else 0, int(b), int(ctas_per_sm), int(lag))
+            _check(lib.paco_plan_create_batched_ex(ctypes.byref(h), arr, n, C64, ctypes.byref(o)))
+        self._h = h
+        inf = PlanInfo()
+        _check(lib.paco_plan_info(self._h, ctypes.byref(inf)))
+        self.info = inf
+        self.lengths = [int(v) for v in lengths]
+        self.N, self.count, self.dtype = inf.N, inf.batch, C64
+
+    def config(self, length: int):
+        """(b, N1, ctas_per_sm, lag) the plan uses for `length`."""
+        b, n1, c, lag = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib.paco_plan_batched_config(self._h, int(length), ctypes.byref(b), ctypes.byref(n1),
+                                            ctypes.byref(c), ctypes.byref(lag)))
+        return b.value, n1.value, c.value, lag.value
 
 
 _PLANS: dict = {}

@@ -17,6 +17,7 @@
 #include <string>
 
 #include "../../include/paco.h"
+#include "paco_plan.h"
 #include "paco_common.cuh"
 #include "paco_panel.cuh"
 #include "paco_stage.cuh"
@@ -37,7 +38,7 @@ using namespace paco;
 // ---------------------------------------------------------------------------
 static thread_local std::string g_last_error;
 
-static paco_status_t fail(paco_status_t st, const char *fmt, ...)
+paco_status_t paco::fail(paco_status_t st, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -47,13 +48,6 @@ static paco_status_t fail(paco_status_t st, const char *fmt, ...)
     g_last_error = buf;
     return st;
 }
-
-#define PACO_CUDA_TRY(call)                                                              \
-    do {                                                                                 \
-        cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess)                                                           \
-            return fail(PACO_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
-    } while (0)
 
 extern "C" const char *paco_last_error(void) { return g_last_error.c_str(); }
 
@@ -65,36 +59,7 @@ extern "C" const char *paco_version(void) { return "paco-gb300 0.1"; }
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
-struct StageCfg {
-    int lgL = 0;      // log2 of the transform length of this stage
-    int lgW = 0;      // log2 tile width
-    int lgK = 0;      // log2 cluster size
-    int threads = 0;
-    int smem = 0;     // dynamic shared memory, bytes
-    int ntiles = 0;   // column tiles per transform
-    const void *fn = nullptr;
-    int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
-    int P = 0;        // panel width (columns)
-};
-
-struct paco_plan {
-    int64_t N1 = 0, N2 = 0, N = 0, batch = 0;
-    int b = 0, t = 0, p = 0, m1 = 0, m2 = 0;
-    paco_dtype_t dtype = PACO_C64;
-    int esize = 8;                 // bytes per complex element
-    int device = 0;
-    StageCfg st[2];                // stage 1 (L = N1, C = N2), stage 2 (L = N2, C = N1)
-    StageCfg ph1;                  // Phase I alone (mode 3), same geometry as st[0]
-    void *twL1 = nullptr, *twL2 = nullptr, *twN_lo = nullptr, *twN_hi = nullptr;
-    int twN_lo_bits = 0;
-    int *d_status = nullptr;
-    void *scratch = nullptr;       // panel ring buffers (L2-sized, not N-sized)
-    unsigned *ctr = nullptr;       // panel pipeline counters
-    size_t ctr_words = 0;
-    int num_sms = 0;
-};
-
-static int ilog2_exact(int64_t v)
+int paco::ilog2_exact(int64_t v)
 {
     if (v <= 0 || (v & (v - 1))) return -1;
     int l = 0;
@@ -114,17 +79,17 @@ __global__ void twiddle_gen_kernel(cx<R> *out, long long M, long long count, lon
     out[r] = make_cx<R>((R)c, (R)(-s));
 }
 
-static paco_status_t gen_table(paco_plan *pl, void **dst, long long M, long long count,
-                               long long mult)
+paco_status_t paco::gen_table(int esize, void **dst, long long M, long long count, long long mult,
+                              cudaStream_t stream)
 {
-    size_t bytes = (size_t)count * (size_t)pl->esize;
+    size_t bytes = (size_t)count * (size_t)esize;
     PACO_CUDA_TRY(cudaMalloc(dst, bytes));
     int threads = 256;
     long long blocks = (count + threads - 1) / threads;
-    if (pl->esize == 8)
-        twiddle_gen_kernel<float><<<(unsigned)blocks, threads>>>((cx<float> *)*dst, M, count, mult);
+    if (esize == 8)
+        twiddle_gen_kernel<float><<<(unsigned)blocks, threads, 0, stream>>>((cx<float> *)*dst, M, count, mult);
     else
-        twiddle_gen_kernel<double><<<(unsigned)blocks, threads>>>((cx<double> *)*dst, M, count, mult);
+        twiddle_gen_kernel<double><<<(unsigned)blocks, threads, 0, stream>>>((cx<double> *)*dst, M, count, mult);
     PACO_CUDA_TRY(cudaGetLastError());
     return PACO_OK;
 }
@@ -256,10 +221,10 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
     const int lgN = l1 + l2;
     pl->twN_lo_bits = (lgN + 1) / 2;
     const long long nlo = 1LL << pl->twN_lo_bits, nhi = (1LL << lgN) / nlo;
-    if ((st = gen_table(pl, &pl->twL1, pl->N1, pl->N1, 1)) != PACO_OK ||
-        (st = gen_table(pl, &pl->twL2, pl->N2, pl->N2, 1)) != PACO_OK ||
-        (st = gen_table(pl, &pl->twN_lo, pl->N, nlo, 1)) != PACO_OK ||
-        (st = gen_table(pl, &pl->twN_hi, pl->N, nhi, nlo)) != PACO_OK) {
+    if ((st = gen_table(pl->esize, &pl->twL1, pl->N1, pl->N1, 1, 0)) != PACO_OK ||
+        (st = gen_table(pl->esize, &pl->twL2, pl->N2, pl->N2, 1, 0)) != PACO_OK ||
+        (st = gen_table(pl->esize, &pl->twN_lo, pl->N, nlo, 1, 0)) != PACO_OK ||
+        (st = gen_table(pl->esize, &pl->twN_hi, pl->N, nhi, nlo, 0)) != PACO_OK) {
         paco_plan_destroy(pl);
         return st;
     }
@@ -312,6 +277,7 @@ extern "C" paco_plan_t *paco_plan_create(int64_t N1, int64_t N2, int b, int64_t 
 extern "C" void paco_plan_destroy(paco_plan_t *pl)
 {
     if (!pl) return;
+    batched_destroy(pl->bs);
     cudaFree(pl->twL1);
     cudaFree(pl->twL2);
     cudaFree(pl->twN_lo);
@@ -326,6 +292,10 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
 {
     if (!pl || !info) return fail(PACO_ERR_INVALID_ARG, "NULL argument");
     memset(info, 0, sizeof(*info));
+    if (pl->bs) {
+        batched_info(pl, info);
+        return PACO_OK;
+    }
     info->N1 = pl->N1; info->N2 = pl->N2; info->N = pl->N; info->batch = pl->batch;
     info->b = pl->b; info->p = pl->p; info->m1 = pl->m1; info->m2 = pl->m2;
     info->dtype = pl->dtype;
@@ -568,6 +538,7 @@ extern "C" paco_status_t paco_execute(paco_plan_t *pl, const void *in, void *out
     if (st != PACO_OK || pl->batch == 0) return st;
     set_device(pl);
     cudaStream_t s = (cudaStream_t)stream;
+    if (pl->bs) return batched_execute(pl, in, out, dir, s);
     if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s)) != PACO_OK) return st;
     return launch_stage(pl, pl->st[1], 2, out, out, dir, s);
 }
@@ -577,6 +548,7 @@ extern "C" paco_status_t paco_execute_stage1(paco_plan_t *pl, const void *in, vo
 {
     paco_status_t st = check_exec(pl, in, W, dir, false);
     if (st != PACO_OK || pl->batch == 0) return st;
+    if (pl->bs) return fail(PACO_ERR_UNSUPPORTED, "%s takes a single-length plan", "paco_execute_stage1");
     set_device(pl);
     return launch_stage(pl, pl->st[0], 1, in, W, dir, (cudaStream_t)stream);
 }
@@ -586,6 +558,7 @@ extern "C" paco_status_t paco_execute_stage2(paco_plan_t *pl, const void *W, voi
 {
     paco_status_t st = check_exec(pl, W, out, dir, true);
     if (st != PACO_OK || pl->batch == 0) return st;
+    if (pl->bs) return fail(PACO_ERR_UNSUPPORTED, "%s takes a single-length plan", "paco_execute_stage2");
     set_device(pl);
     return launch_stage(pl, pl->st[1], 2, W, out, dir, (cudaStream_t)stream);
 }
@@ -595,6 +568,7 @@ extern "C" paco_status_t paco_execute_phase1(paco_plan_t *pl, const void *in, vo
 {
     paco_status_t st = check_exec(pl, in, out, dir, false);
     if (st != PACO_OK || pl->batch == 0) return st;
+    if (pl->bs) return fail(PACO_ERR_UNSUPPORTED, "%s takes a single-length plan", "paco_execute_phase1");
     set_device(pl);
     return launch_stage(pl, pl->ph1, 3, in, out, dir, (cudaStream_t)stream);
 }
@@ -602,8 +576,11 @@ extern "C" paco_status_t paco_execute_phase1(paco_plan_t *pl, const void *in, vo
 extern "C" paco_status_t paco_permute(paco_plan_t *pl, const void *A_tilde, void *W, int dir,
                                       paco_stream_t stream)
 {
-    (void)pl; (void)A_tilde; (void)W; (void)dir; (void)stream;
-    return fail(PACO_ERR_UNSUPPORTED, "paco_permute is not built yet");
+    paco_status_t st = check_exec(pl, A_tilde, W, dir, false);
+    if (st != PACO_OK || pl->batch == 0) return st;
+    if (pl->bs) return fail(PACO_ERR_UNSUPPORTED, "paco_permute takes a single-length plan");
+    set_device(pl);
+    return launch_permute(pl, A_tilde, W, dir, (cudaStream_t)stream);
 }
 
 extern "C" paco_status_t paco_execute_host(paco_plan_t *pl, const void *h_in, void *h_out,

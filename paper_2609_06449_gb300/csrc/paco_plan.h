@@ -1,0 +1,72 @@
+// paco_plan.h -- host-side plan state shared by the library's translation
+// units (not part of the C ABI; include/paco.h is the public interface).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/paco.h"
+
+namespace paco {
+
+struct StageCfg {
+    int lgL = 0;      // log2 of the transform length of this stage
+    int lgW = 0;      // log2 tile width
+    int lgK = 0;      // log2 cluster size
+    int threads = 0;
+    int smem = 0;     // dynamic shared memory, bytes
+    int ntiles = 0;   // column tiles per transform
+    const void *fn = nullptr;
+    int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
+    int P = 0;        // panel width (columns)
+};
+
+struct BatchedState;  // paco_batched.cu
+
+} // namespace paco
+
+struct paco_plan {
+    int64_t N1 = 0, N2 = 0, N = 0, batch = 0;
+    int b = 0, t = 0, p = 0, m1 = 0, m2 = 0;
+    paco_dtype_t dtype = PACO_C64;
+    int esize = 8;                 // bytes per complex element
+    int device = 0;
+    paco::StageCfg st[2];          // stage 1 (L = N1, C = N2), stage 2 (L = N2, C = N1)
+    paco::StageCfg ph1;            // Phase I alone (mode 3), same geometry as st[0]
+    void *twL1 = nullptr, *twL2 = nullptr, *twN_lo = nullptr, *twN_hi = nullptr;
+    int twN_lo_bits = 0;
+    int *d_status = nullptr;
+    void *scratch = nullptr;       // panel ring buffers (L2-sized, not N-sized)
+    unsigned *ctr = nullptr;       // panel pipeline counters
+    size_t ctr_words = 0;
+    int num_sms = 0;
+    // uneven batch (paco_plan_create_batched): N = total elements, batch = 1
+    paco::BatchedState *bs = nullptr;
+};
+
+namespace paco {
+
+paco_status_t fail(paco_status_t st, const char *fmt, ...);
+int ilog2_exact(int64_t v);
+// FP64-generated table of w_M^{-(r*mult)}, r in [count], complex of `esize` bytes
+paco_status_t gen_table(int esize, void **dst, long long M, long long count, long long mult,
+                        cudaStream_t stream);
+
+// paco_permute.cu
+paco_status_t launch_permute(const paco_plan *pl, const void *A_tilde, void *W, int dir,
+                             cudaStream_t stream);
+
+// paco_batched.cu
+paco_status_t batched_execute(paco_plan *pl, const void *in, void *out, int dir, cudaStream_t stream);
+void batched_destroy(BatchedState *bs);
+void batched_info(const paco_plan *pl, paco_plan_info_t *info);
+
+} // namespace paco
+
+#define PACO_CUDA_TRY(call)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return ::paco::fail(PACO_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)

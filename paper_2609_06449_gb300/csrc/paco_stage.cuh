@@ -65,6 +65,21 @@ __device__ __forceinline__ cx<double> ldg_cx<double>(const cx<double> *p)
 }
 
 template <typename R>
+__device__ __forceinline__ cx<R> ldcg_cx(const cx<R> *p);
+template <>
+__device__ __forceinline__ cx<float> ldcg_cx<float>(const cx<float> *p)
+{
+    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    return make_cx<float>(v.x, v.y);
+}
+template <>
+__device__ __forceinline__ cx<double> ldcg_cx<double>(const cx<double> *p)
+{
+    double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+    return make_cx<double>(v.x, v.y);
+}
+
+template <typename R>
 __device__ __forceinline__ void st_cx(cx<R> *p, cx<R> v) { *p = v; }
 
 // Dynamic shared memory needed by a stage CTA (elements of cx<R>).
@@ -84,8 +99,14 @@ __host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int 
 // LGWC, LGKC, MC > 0 fix log2 W, log2 K and the mode at compile time (the
 // hot configurations); 0 takes them from args at run time.  MINB is the
 // minimum number of resident CTAs per SM requested from the compiler.
-template <typename R, int A, int B, int LGWC = -1, int LGKC = -1, int MC = 0, int MINB = 1>
-__global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs args)
+//
+// stage_tile is the body: one tile (`tile`, transform base offset `boff`,
+// cluster rank `rank`) computed by the calling CTA's NT = NE / EPT threads.
+// LDCG loads the tile input through L2 only (ld.global.cg): for inputs that
+// other CTAs of the same launch wrote (the batched persistent kernel).
+template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG>
+__device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long long boff, int rank,
+                                           unsigned char *smem_raw)
 {
     using C = cx<R>;
     constexpr int L = A * B;
@@ -101,8 +122,6 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs a
     static_assert(EPT % RA1 == 0 && EPT % RB1 == 0, "radix must divide EPT");
     static_assert(RA2 == 1 || EPT % RA2 == 0, "radix must divide EPT");
     static_assert(RB2 == 1 || EPT % RB2 == 0, "radix must divide EPT");
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
 
     const int lgW = (LGWC >= 0) ? LGWC : args.lgW;
     const int lgK = (LGKC >= 0) ? LGKC : args.lgK;
@@ -124,10 +143,6 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs a
     C *E2 = E1 + Ak * W;          // mode 1: w_N^{-A k_hi c}   [B][W]
 
     const int tid = threadIdx.x;
-    int rank = 0;
-    if (K > 1) rank = (int)cg::this_cluster().block_rank();
-    const int tile = blockIdx.x >> lgK;
-    const long long boff = (long long)blockIdx.y * args.batch_stride;
     const int c0 = tile << lgW;
     const R csign = args.conj ? R(-1) : R(1);
 
@@ -178,7 +193,8 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs a
                 const int j = (jj + RA2 * r) * B + jlo;       // logical row in [L]
                 const unsigned row = (mode == 2) ? digit_reverse((unsigned)j, args.rev_bits, args.rev_t)
                                                  : (unsigned)j;
-                C x = ldg_cx(gin + (long long)row * args.C + c0 + col);
+                C x = LDCG ? ldcg_cx(gin + (long long)row * args.C + c0 + col)
+                           : ldg_cx(gin + (long long)row * args.C + c0 + col);
                 x.y *= csign;
                 v[u * RA1 + r] = x;
             }
@@ -330,6 +346,17 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs a
             st_cx(gout + idx, y);
         }
     }
+}
+
+template <typename R, int A, int B, int LGWC = -1, int LGKC = -1, int MC = 0, int MINB = 1>
+__global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lgK = (LGKC >= 0) ? LGKC : args.lgK;
+    int rank = 0;
+    if ((1 << lgK) > 1) rank = (int)cg::this_cluster().block_rank();
+    stage_tile<R, A, B, LGWC, LGKC, MC, false>(args, (int)(blockIdx.x >> lgK),
+                                               (long long)blockIdx.y * args.batch_stride, rank, smem_raw);
 }
 
 // L = A (B == 1): the whole transform is F1; store straight from F1's layout.

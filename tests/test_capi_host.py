@@ -73,3 +73,28 @@ def test_plan_rejects_negative_batch_and_bad_dtype():
         paco.Plan(16, 16, 2, -1, paco.C64)
     with pytest.raises(paco.PacoError):
         paco.Plan(16, 16, 2, 1, 9)
+
+
+@pytest.mark.parametrize("lengths,msg", [
+    ([256, 48], "powers of two"),
+    ([8], "powers of two"),            # below 2^4
+    ([2 ** 21], "powers of two"),      # above 2^20
+])
+def test_batched_plan_rejects_unsupported_lengths(lengths, msg):
+    import paper_2609_06449_gb300 as paco
+    with pytest.raises(paco.PacoError) as ei:
+        paco.BatchedPlan(lengths)
+    assert msg in str(ei.value) and ei.value.status == 2
+
+
+def test_batched_plan_rejects_bad_arguments():
+    import paper_2609_06449_gb300 as paco
+    L = paco.lib
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 2)(256, 1024)
+    assert L.paco_plan_create_batched(ctypes.byref(h), arr, 2, paco.C128) == 2   # dtype
+    assert L.paco_plan_create_batched(ctypes.byref(h), None, 3, paco.C64) == 1   # NULL list
+    assert L.paco_plan_create_batched(ctypes.byref(h), arr, -1, paco.C64) == 1
+    o = paco.BatchedOpts(0, 3, 1, 0)                                             # radix 3
+    assert L.paco_plan_create_batched_ex(ctypes.byref(h), arr, 2, paco.C64, ctypes.byref(o)) == 1
+    assert L.paco_plan_batched_config(None, 256, None, None, None, None) == 1

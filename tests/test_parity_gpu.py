@@ -226,3 +226,44 @@ def test_full_size_complex128():
         assert err <= 1e-14 * 27, f"dir={d} rel_l2={err:.3e}"
     del xd, yd
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", [paco.C64, paco.C128])
+@pytest.mark.parametrize("N1,N2,b,p", [(2, 8, 2, 2), (16, 16, 4, 4), (64, 16, 2, 2), (16, 64, 4, 4),
+                                       (256, 256, 2, 4), (512, 64, 8, 8), (128, 512, 2, 8),
+                                       (4096, 64, 4, 16), (16384, 256, 4, 4), (256, 16384, 4, 4)])
+def test_unfused_pipeline(N1, N2, b, p, dtype):
+    """Phase I alone -> paco_permute (PARA-CO-DRP as its own pass) -> Phase
+    III equals the transform; the permuted array equals Z-hat of Eq. (17)
+    from the simulator and the fused stage-1 output."""
+    N = N1 * N2
+    batch = 2 if N <= 2 ** 16 else 1
+    x = gaussian(batch * N, 5, NP[dtype]).reshape(batch, N)
+    plan = paco.Plan(N1, N2, b, batch, dtype, p=p)
+    tol = TOL[dtype] * max(1.0, math.log2(N))
+    xt = torch.from_numpy(x).cuda()
+    for d in (-1, 1):
+        At = torch.empty_like(xt)
+        W = torch.empty_like(xt)
+        Wf = torch.empty_like(xt)
+        y = torch.empty_like(xt)
+        plan.execute_phase1(xt, At, d)
+        plan.permute(At, W, d)
+        plan.execute_stage1(xt, Wf, d)
+        plan.execute_stage2(W, y, d)
+        torch.cuda.synchronize()
+        plan.check()
+        ref = oracle.fft(x.astype(np.complex128), dir=d)
+        assert rel_l2(y.cpu().numpy(), ref) <= tol
+        Wn, Wfn = W.cpu().numpy(), Wf.cpu().numpy()
+        assert rel_l2(Wn, Wfn.astype(np.complex128)) <= tol
+        if d == -1:
+            sim = ps.simulate(x[0].astype(np.complex128), N1, N2, b, p, phase1="lemma")
+            assert rel_l2(Wn[0].reshape(1, -1), sim["W"].reshape(1, -1)) <= tol
+
+
+def test_permute_rejects_aliasing():
+    plan = paco.Plan(64, 64, 2, 1, paco.C64)
+    xt = torch.zeros(4096, dtype=torch.complex64, device="cuda")
+    with pytest.raises(paco.PacoError):
+        plan.permute(xt, xt)
