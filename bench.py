@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the PACO hot path on GB300.
 
-Workload: one complex64 1-D DFT of N = 2^28 as N1 = N2 = 2^14, radix b = 4,
-p = 64 virtual slabs, forward (w^{-kj}); input Re/Im i.i.d. U[-1, 1) from
-seed (rank).  One step = one pass of the whole path: Phase I with the fused
-twiddle + digit-reversal redistribution (stage 1), then Phase III (stage 2),
-exactly the two launches paco_execute makes.  The input (2 GiB) is larger
-than L2, so no flush is needed between steps.
+Default workload (the headline): one complex64 1-D DFT of N = 2^28 as
+N1 = N2 = 2^14, radix b = 4, p = 64 virtual slabs, forward (w^{-kj}); input
+Re/Im i.i.d. U[-1, 1) from seed (rank).  One step = one pass of the whole
+path: Phase I with the fused twiddle + digit-reversal redistribution
+(stage 1), then Phase III (stage 2), exactly the two launches paco_execute
+makes.  The input (2 GiB) is larger than L2, so no flush is needed between
+steps.  The same line carries the tensor-core sub-DFT forms (BF16x3 split,
+FP16 per-block scaled) timed on the same transform, each with its relative
+L2 error against the FP64 oracle.
 
 Reported: 5 N log2 N GFLOP/s (whole job), effective HBM GB/s (32 N bytes per
 step: two reads and two writes of N complex64), the dominant kernel's
@@ -14,7 +17,13 @@ roofline against the measured copy bandwidth, an end-to-end number through
 paco_execute_host with pinned host buffers, the CPU oracle on a bounded
 sample, and SM clocks sampled during the timed region.
 
+Other workloads (--workload): A (2^16 as 256 x 256, latency), B128
+(complex128 N = 2^27), C (the uneven batch in one persistent launch), D
+(16 x 2^24 per precision form), E (forward + backward of 256 x 2^20 through
+the autograd function).  Each prints one line of the same contract.
+
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paco|reference]
+                  [--workload B|A|B128|C|D|E]
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 transform does not shard across GPUs on this path); timing is the max over
@@ -57,6 +66,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["B", "A", "B128", "C", "D", "E"], default="B")
+    ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core forms on the headline line")
     return ap.parse_args()
 
 
@@ -273,6 +284,341 @@ def measured_peak_hbm():
 
 
 # ---------------------------------------------------------------------------
+# shared pieces of the GPU leg
+# ---------------------------------------------------------------------------
+def time_steps(step, K: int, warmup: int, stream):
+    """Warm up, then time exactly K steps with one CUDA event pair per step on
+    `stream`; returns (total ms from the first step's start to the last
+    step's end, list of per-step ms)."""
+    import torch
+    for _ in range(max(warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    for k in range(K):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    per = [a.elapsed_time(b) for a, b in ev]
+    return ev[0][0].elapsed_time(ev[K - 1][1]), per
+
+
+def rel_l2_vs_oracle(y, x):
+    import numpy as np
+
+    import oracle
+    ref = oracle.fft(np.asarray(x, dtype=np.complex128).reshape(1, -1), threads=0)
+    got = np.asarray(y, dtype=np.complex128).reshape(ref.shape)
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def form_errors(paco, forms, lg1: int = 12, lg2: int = 12, b: int = 4):
+    """Relative L2 error of each form against the FP64 oracle on one
+    2^(lg1+lg2)-point transform of the headline recipe (U[-1,1), seed 0)."""
+    import numpy as np
+    import torch
+
+    from paco_inputs import uniform
+    N1, N2 = 1 << lg1, 1 << lg2
+    x = uniform(N1 * N2, 0, np.complex64)
+    xt = torch.from_numpy(x).cuda()
+    out = {}
+    for name, dt in forms:
+        pl = paco.Plan(N1, N2, b, 1, dt)
+        y = torch.empty_like(xt)
+        pl.execute(xt, y, -1)
+        torch.cuda.synchronize()
+        pl.check()
+        out[name] = rel_l2_vs_oracle(y.cpu().numpy(), x)
+        pl.close()
+    return out
+
+
+def tc_split(paco, x, y, N1, N2, b, p, K, warmup, stream, flop, world, max_over_ranks):
+    """The tensor-core sub-DFT forms on the headline transform: time per step
+    (two launches of the TC stage kernel) and error at 2^24 against the
+    oracle, next to the plain form's error."""
+    res = {}
+    KT = max(min(K, 50), 5)
+    for name, dt in (("bf16x3", paco.C64_TC_BF16X3), ("fp16", paco.C64_TC_FP16)):
+        pl = paco.Plan(N1, N2, b, 1, dt, p=p)
+        tot, per = time_steps(lambda: pl.execute(x, y, -1, stream), KT, warmup, stream)
+        pl.check()
+        ms = max_over_ranks(tot) / KT
+        res[name] = {"ms_per_step": ms, "value": flop * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+                     "steps": KT, "kernel": "paco_stage_kernel, radix-16 passes as mma.sync contractions"}
+        pl.close()
+    errs = form_errors(paco, [("plain", paco.C64), ("bf16x3", paco.C64_TC_BF16X3),
+                              ("fp16", paco.C64_TC_FP16)])
+    for k, v in errs.items():
+        res.setdefault(k, {})["rel_l2"] = v
+    res["error_measured_on"] = "one 2^24 transform (4096 x 4096, b=4), U[-1,1) seed 0, vs the FP64 oracle"
+    return res
+
+
+def cpu_leg(args, rank, world, dtype="c64", lg=None):
+    if rank != 0 or world != 1 or args.no_cpu_baseline:
+        return None
+    lg = args.cpu_lg if lg is None else lg
+    try:
+        g, per, reps = oracle_sample(lg, args.cpu_seconds, dtype)
+        return {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                "sample": f"{reps} x one 2^{lg}-point transform (same recipe), "
+                          f"FP64 recursive radix-2 oracle, 1 thread, {per:.2f} s each"}
+    except Exception as e:  # report, do not hide
+        return {"value": None, "unit": "GFLOP/s", "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
+
+
+def hbm_roofline(kernel, bytes_per_launch, ms_per_launch, traffic=None):
+    peak, src = measured_peak_hbm()
+    achieved = bytes_per_launch / (ms_per_launch * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "peak_source": src,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_per_launch}
+
+
+def e2e_host(step_host, KE, stream, units, unit, h2d, d2h, api, max_over_ranks, world, barrier):
+    import torch
+    for _ in range(2):
+        step_host()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(KE):
+        step_host()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e_ms = max_over_ranks(a.elapsed_time(b)) / KE
+    return {"value": units * world / (e_ms * 1e-3), "unit": unit, "ms_per_step": e_ms,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "api": api}
+
+
+def emit(line):
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# other workloads
+# ---------------------------------------------------------------------------
+def run_other(args, ranks, local):
+    import numpy as np
+    import torch
+
+    import paper_2609_06449_gb300 as paco
+    from paco_inputs import gaussian, uniform, uneven_lengths
+
+    rank, world = ranks.rank, ranks.world
+    stream = torch.cuda.current_stream()
+    K = args.steps
+    W = max(args.warmup, 3)
+    sampler = ClockSampler(local)
+    mor = ranks.max_over_ranks
+    base = {"n_gpus": world, "steps": K, "warmup": W, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic", "metric": METRIC}
+
+    def timed(step):
+        sampler.start()
+        time.sleep(0.3)
+        ranks.barrier()
+        torch.cuda.synchronize()
+        t0 = time.time()
+        tot, per = time_steps(step, K, 0, stream)
+        t1 = time.time()
+        ranks.barrier()
+        return tot, per, sampler.stop(t0, t1)
+
+    wl = args.workload
+    if wl == "A":
+        N1 = N2 = 256
+        N = N1 * N2
+        plan = paco.Plan(N1, N2, 2, 1, paco.C64, p=4)
+        xh = torch.from_numpy(uniform(N, rank, np.complex64)).pin_memory()
+        x = xh.cuda()
+        y = torch.empty_like(x)
+        for _ in range(W):
+            plan.execute(x, y, -1, stream)
+        tot, per, clocks = timed(lambda: plan.execute(x, y, -1, stream))
+        plan.check()
+        us = mor(statistics.median(per)) * 1e3
+        ho = torch.empty_like(xh).pin_memory()
+        di = torch.empty_like(x)
+        e2e = e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 20), stream,
+                       1.0, "transforms/s", N * 8, N * 8, "paco_execute_host (pinned host buffers)", mor, world,
+                       ranks.barrier)
+        line = dict(base, value=us, unit="us (median latency per transform)", higher_is_better=False,
+                    ms_per_step=mor(tot) / K, dtype="f32",
+                    config={"workload": "c64 1-D DFT N=2^16 as 256 x 256, b=2, p=4, forward, latency",
+                            "N1": N1, "N2": N2, "b": 2, "p": 4, "batch": 1,
+                            "input": "Re, Im i.i.d. U[-1,1), seed = rank",
+                            "l2": "input fits in L2: latency-bound by design, no flush"},
+                    roofline=dict(hbm_roofline("stage kernels (2 launches)", 32.0 * N, statistics.median(per)),
+                                  bound="latency"),
+                    gflops=5.0 * N * 16 / (us * 1e-6) / 1e9,
+                    e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=16), gpu_launches=2 * K, clocks=clocks)
+    elif wl == "B128":
+        N1, N2 = 1 << 13, 1 << 14
+        N = N1 * N2
+        plan = paco.Plan(N1, N2, 2, 1, paco.C128, p=128)
+        xh = torch.from_numpy(uniform(N, rank, np.complex128)).pin_memory()
+        x = xh.cuda()
+        y = torch.empty_like(x)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+
+        def step2(k=[0]):
+            i = k[0] % K
+            ev[i][0].record(stream)
+            plan.execute_stage1(x, y, -1, stream)
+            ev[i][1].record(stream)
+            plan.execute_stage2(y, y, -1, stream)
+            ev[i][2].record(stream)
+            k[0] += 1
+        for _ in range(W):
+            plan.execute(x, y, -1, stream)
+        tot, per, clocks = timed(step2)
+        plan.check()
+        s1 = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(K))
+        s2 = statistics.mean(ev[k][1].elapsed_time(ev[k][2]) for k in range(K))
+        flop = 5.0 * N * 27
+        ms = mor(tot) / K
+        fp64_peak = 1250.0
+        dom_ms = max(s1, s2)
+        ho = torch.empty_like(xh).pin_memory()
+        di = torch.empty_like(x)
+        e2e = e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1), stream,
+                       flop / 1e9, "GFLOP/s", N * 16, N * 16, "paco_execute_host (pinned host buffers)", mor,
+                       world, ranks.barrier)
+        hr = hbm_roofline("stage1" if s1 >= s2 else "stage2", 32.0 * N, dom_ms)
+        line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s", higher_is_better=True,
+                    ms_per_step=ms, dtype="f64",
+                    config={"workload": "c128 1-D DFT N=2^27 as N1=2^13 x N2=2^14, b=2, p=128, forward",
+                            "N1": N1, "N2": N2, "b": 2, "p": 128, "batch": 1,
+                            "input": "Re, Im i.i.d. U[-1,1), seed = rank", "l2": "inputs larger than L2"},
+                    stage_ms={"stage1": s1, "stage2": s2}, hbm_gbs_effective=64.0 * N * world / (ms * 1e-3) / 1e9,
+                    roofline={"bound": "alu", "kernel": hr["kernel"],
+                              "achieved": flop / 2 / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak / 1e3,
+                              "unit": "TFLOP/s (nominal 5N log2 N flops, half per stage)",
+                              "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                              "frac": flop / 2 / (dom_ms * 1e-3) / 1e12 / (fp64_peak / 1e3),
+                              "traffic": None, "hbm": hr},
+                    e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, "c128"), gpu_launches=2 * K, clocks=clocks)
+    elif wl == "C":
+        e = uneven_lengths()
+        lengths = np.concatenate([2 ** e, np.full(2 ** 14, 2 ** 12)]).astype(np.int64)
+        total = int(lengths.sum())
+        t_plan = time.time()
+        plan = paco.BatchedPlan(lengths)
+        t_plan = time.time() - t_plan
+        xh = torch.from_numpy(gaussian(total, rank, np.complex64)).pin_memory()
+        x = xh.cuda()
+        y = torch.empty_like(x)
+        for _ in range(W):
+            plan.execute(x, y, -1, stream)
+        tot, per, clocks = timed(lambda: plan.execute(x, y, -1, stream))
+        plan.check()
+        flop = float(np.sum(5.0 * lengths * np.log2(lengths)))
+        ms = mor(tot) / K
+        ho = torch.empty_like(xh).pin_memory()
+        di = torch.empty_like(x)
+        e2e = e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1), stream,
+                       flop / 1e9, "GFLOP/s", total * 8, total * 8, "paco_execute_host (pinned host buffers)", mor,
+                       world, ranks.barrier)
+        cfg = {str(int(n)): dict(zip(("b", "N1", "ctas_per_sm", "lag"), plan.config(int(n))))
+               for n in np.unique(lengths)}
+        line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s", higher_is_better=True,
+                    ms_per_step=ms, dtype="f32",
+                    config={"workload": "uneven batch: 4096 c64 transforms, log2 lengths uniform over 8..20 "
+                                        "reduced to a 2^28 total, plus 2^14 transforms of 2^12; one persistent "
+                                        "launch", "transforms": int(len(lengths)), "total_elements": total,
+                            "input": "Re, Im i.i.d. N(0,1), seed = rank", "l2": "inputs larger than L2",
+                            "autotuned": cfg, "plan_seconds": t_plan},
+                    hbm_gbs_effective=32.0 * total * world / (ms * 1e-3) / 1e9,
+                    roofline=hbm_roofline("paco_batched_kernel (1 launch)", 16.0 * total, statistics.mean(per)),
+                    e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=18), gpu_launches=K, clocks=clocks)
+    elif wl == "D":
+        N1 = N2 = 4096
+        N, B = N1 * N2, 16
+        xh = torch.from_numpy(np.concatenate([
+            __import__("paco_inputs").loguniform(N, 100 * rank + i, np.complex64) for i in range(B)])).pin_memory()
+        x = xh.cuda()
+        y = torch.empty_like(x)
+        flop = 5.0 * N * 24 * B
+        forms = {}
+        clocks = None
+        for name, dt in (("plain", paco.C64), ("bf16x3", paco.C64_TC_BF16X3), ("fp16", paco.C64_TC_FP16)):
+            pl = paco.Plan(N1, N2, 4, B, dt)
+            for _ in range(W):
+                pl.execute(x, y, -1, stream)
+            tot, per, ck = timed(lambda: pl.execute(x, y, -1, stream))
+            pl.check()
+            ms = mor(tot) / K
+            torch.cuda.synchronize()
+            err = rel_l2_vs_oracle(y[:N].cpu().numpy(), xh[:N].numpy())
+            forms[name] = {"ms_per_step": ms, "value": flop * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+                           "rel_l2_transform0": err, "dominant_launch_ms": statistics.mean(per) / 2}
+            if name == "bf16x3":
+                clocks = ck
+            pl.close()
+        line = dict(base, value=forms["bf16x3"]["value"], unit="GFLOP/s", higher_is_better=True,
+                    ms_per_step=forms["bf16x3"]["ms_per_step"], dtype="bf16x3 operands, f32 accumulate",
+                    config={"workload": "16 x c64 1-D DFT N=2^24 (4096 x 4096, b=4), forward; precision forms",
+                            "input": "log-uniform magnitudes 1e-4..1e4, uniform phases, seed = 100*rank + i",
+                            "l2": "inputs larger than L2"},
+                    forms=forms,
+                    roofline=hbm_roofline("TC stage kernel (bf16x3)", 16.0 * N * B,
+                                          forms["bf16x3"]["dominant_launch_ms"]),
+                    e2e=None, cpu_baseline=cpu_leg(args, rank, world), gpu_launches=2 * K * 3, clocks=clocks)
+        # e2e for the headline form of this line
+        pl = paco.Plan(N1, N2, 4, B, paco.C64_TC_BF16X3)
+        ho = torch.empty_like(xh).pin_memory()
+        di = torch.empty_like(x)
+        line["e2e"] = e2e_host(lambda: pl.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1),
+                               stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
+                               "paco_execute_host (pinned host buffers)", mor, world, ranks.barrier)
+    else:  # E
+        N1 = N2 = 1024
+        N, B = N1 * N2, 256
+        xh = torch.from_numpy(gaussian(N * B, rank, np.complex64).reshape(B, N)).pin_memory()
+        wh = torch.from_numpy(__import__("paco_inputs").weights(N * B, rank + 1).reshape(B, N)).pin_memory()
+        x = xh.cuda().requires_grad_(True)
+        w = wh.cuda()
+
+        def step():
+            x.grad = None
+            yv = paco.PacoFFT.apply(x, N1, N2, 4)
+            loss = (w * (yv.real ** 2 + yv.imag ** 2)).sum()
+            loss.backward()
+            return loss
+        for _ in range(W):
+            step()
+        tot, per, clocks = timed(step)
+        flop = 2 * 5.0 * N * 20 * B
+        ms = mor(tot) / K
+        gh = torch.empty_like(xh).pin_memory()
+
+        def step_host():
+            xd = xh.to("cuda", non_blocking=True).requires_grad_(True)
+            yv = paco.PacoFFT.apply(xd, N1, N2, 4)
+            loss = (w * (yv.real ** 2 + yv.imag ** 2)).sum()
+            loss.backward()
+            gh.copy_(xd.grad, non_blocking=True)
+        e2e = e2e_host(step_host, max(args.e2e_steps, 1), stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
+                       "torch.autograd through PacoFFT (pinned host input and gradient)", mor, world, ranks.barrier)
+        line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s (forward + backward transforms)",
+                    higher_is_better=True, ms_per_step=ms, dtype="f32",
+                    config={"workload": "256 x c64 1-D DFT N=2^20 (1024 x 1024, b=4): loss = sum(w |FFT(x)|^2), "
+                                        "forward + backward (conjugate transform) through torch.autograd",
+                            "input": "x Re, Im i.i.d. N(0,1); w U[0,1)", "l2": "inputs larger than L2"},
+                    roofline=hbm_roofline("stage kernels (4 launches + torch loss ops)", 4 * 16.0 * N * B, ms),
+                    e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=20), gpu_launches=4 * K, clocks=clocks)
+    if rank == 0:
+        emit(line)
+
+
+# ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
 def main():
@@ -294,6 +640,10 @@ def main():
     torch.cuda.set_device(local)
     ranks = Ranks("nccl", device="cuda")
     barrier, max_over_ranks = ranks.barrier, ranks.max_over_ranks
+    if args.workload != "B":
+        run_other(args, ranks, local)
+        ranks.close()
+        return
 
     N1, N2 = 1 << args.lg1, 1 << args.lg2
     N = N1 * N2
@@ -374,17 +724,12 @@ def main():
                "h2d_bytes_per_step": N * esize, "d2h_bytes_per_step": N * esize,
                "api": "paco_execute_host (pinned host buffers)"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        try:
-            import oracle
-            g, per, reps = oracle_sample(args.cpu_lg, args.cpu_seconds, args.dtype)
-            cpu = {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-                   "sample": f"{reps} x one 2^{args.cpu_lg}-point transform (same recipe), "
-                             f"FP64 recursive radix-2 oracle, 1 thread, {per:.2f} s each"}
-        except Exception as e:  # report, do not hide
-            cpu = {"value": None, "unit": "GFLOP/s", "cores": 0, "kind": "oracle",
-                   "sample": f"failed: {e}"}
+    tc = None
+    if args.dtype == "c64" and not args.no_tc:
+        tc = tc_split(paco, x, out, N1, N2, args.b, args.p, K, args.warmup, stream, flop, world, max_over_ranks)
+        tc["plain"].update({"ms_per_step": ms_step, "value": value, "unit": "GFLOP/s"})
+
+    cpu = cpu_leg(args, rank, world, args.dtype)
 
     if rank == 0:
         line = {
@@ -400,6 +745,7 @@ def main():
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": 2 * K, "clocks": clocks,
+            "tc_split": tc,
         }
         print(json.dumps(line), flush=True)
     ranks.close()

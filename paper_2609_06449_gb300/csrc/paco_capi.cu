@@ -131,7 +131,7 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
                                  int req_w, int req_k)
 {
     sc->lgL = lgL;
-    if (pl->esize == 8 && lgL == 14 && (mode == 1 || mode == 2) && C >= kPanelWidth &&
+    if (!pl->form && pl->esize == 8 && lgL == 14 && (mode == 1 || mode == 2) && C >= kPanelWidth &&
         req_w == 0 && req_k == 0) {
         sc->panel = 1;
         sc->P = kPanelWidth;
@@ -152,9 +152,14 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
     const int EPT = L < 16 ? L : 16;
     const int64_t NE = (int64_t)A * (B / K) * W;     // elements per CTA
     sc->ntiles = (int)(C / W);
-    sc->fn = (pl->esize == 8) ? stage_kernel_fn_special_f32(lgL, sc->lgW, sc->lgK, mode)
-                              : stage_kernel_fn_special_f64(lgL, sc->lgW, sc->lgK, mode);
-    if (!sc->fn) sc->fn = (pl->esize == 8) ? stage_kernel_fn_f32(lgL) : stage_kernel_fn_f64(lgL);
+    if (pl->form) {
+        sc->fn = stage_kernel_fn_tc(lgL, pl->form);
+        if (!sc->fn) return fail(PACO_ERR_UNSUPPORTED, "tensor-core forms need stage lengths 2^8..2^14");
+    } else {
+        sc->fn = (pl->esize == 8) ? stage_kernel_fn_special_f32(lgL, sc->lgW, sc->lgK, mode)
+                                  : stage_kernel_fn_special_f64(lgL, sc->lgW, sc->lgK, mode);
+        if (!sc->fn) sc->fn = (pl->esize == 8) ? stage_kernel_fn_f32(lgL) : stage_kernel_fn_f64(lgL);
+    }
     if (!sc->fn) return fail(PACO_ERR_UNSUPPORTED, "stage length 2^%d is not built (max 2^14)", lgL);
     if (B == 1) {
         sc->threads = W;
@@ -165,6 +170,7 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         const int pad = (mode == 1) ? 1 : W;
         sc->smem = stage_smem_elems(A, B, K, W, pad) * pl->esize;
     }
+    if (pl->form) sc->smem = ((sc->smem + 15) & ~15) + tc_smem_bytes(pl->form, (sc->threads + 31) / 32);
     if (sc->threads > 512 || sc->threads < 1)
         return fail(PACO_ERR_INVALID_ARG, "tile of %lld elements needs %d threads (max 512)",
                     (long long)NE, sc->threads);
@@ -181,7 +187,8 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
     if (!o) return fail(PACO_ERR_INVALID_ARG, "opts is NULL");
     if (o->b != 2 && o->b != 4 && o->b != 8 && o->b != 16)
         return fail(PACO_ERR_INVALID_ARG, "radix b=%d must be 2, 4, 8 or 16", o->b);
-    if (o->dtype != PACO_C64 && o->dtype != PACO_C128)
+    if (o->dtype != PACO_C64 && o->dtype != PACO_C128 && o->dtype != PACO_C64_TC_BF16X3 &&
+        o->dtype != PACO_C64_TC_FP16)
         return fail(PACO_ERR_UNSUPPORTED, "dtype %d is not built", (int)o->dtype);
     if (o->batch < 0) return fail(PACO_ERR_INVALID_ARG, "batch %lld < 0", (long long)o->batch);
     const int t = ilog2_exact(o->b);
@@ -190,6 +197,9 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
     if (l2 < 1 || l2 % t) return fail(PACO_ERR_INVALID_ARG, "N2=%lld is not a power of b=%d (>= b)", (long long)o->N2, o->b);
     if (l1 + l2 > 32) return fail(PACO_ERR_UNSUPPORTED, "N = 2^%d exceeds 2^32", l1 + l2);
     if (l1 > 14 || l2 > 14) return fail(PACO_ERR_UNSUPPORTED, "factors above 2^14 are not built");
+    const bool tc = (o->dtype == PACO_C64_TC_BF16X3 || o->dtype == PACO_C64_TC_FP16);
+    if (tc && (l1 < 8 || l2 < 8))
+        return fail(PACO_ERR_UNSUPPORTED, "tensor-core forms need N1, N2 >= 2^8 (radix-16 passes in both stages)");
     const int m1 = l1 / t, m2 = l2 / t;
     int p = o->p;
     if (p == 0) {
@@ -207,13 +217,21 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
     pl->b = o->b; pl->t = t; pl->p = p; pl->m1 = m1; pl->m2 = m2;
     pl->dtype = o->dtype;
     pl->esize = (o->dtype == PACO_C128) ? 16 : 8;
+    pl->form = (o->dtype == PACO_C64_TC_BF16X3) ? TC_BF16X3 : (o->dtype == PACO_C64_TC_FP16) ? TC_FP16 : TC_NONE;
+    if (pl->form) {
+        paco_status_t ts = tc_table_create(pl->form, &pl->tc);
+        if (ts != PACO_OK) {
+            delete pl;
+            return ts;
+        }
+    }
     cudaGetDevice(&pl->device);
 
     paco_status_t st;
     if ((st = setup_stage(pl, &pl->st[0], l1, pl->N2, 1, o->tile_w, o->cluster)) != PACO_OK ||
         (st = setup_stage(pl, &pl->ph1, l1, pl->N2, 3, o->tile_w, o->cluster)) != PACO_OK ||
         (st = setup_stage(pl, &pl->st[1], l2, pl->N1, 2, o->tile_w, o->cluster)) != PACO_OK) {
-        delete pl;
+        paco_plan_destroy(pl);
         return st;
     }
     // FP64-generated twiddle tables: w_N1^{-r}, w_N2^{-r}, and w_N^{-r} in
@@ -278,6 +296,7 @@ extern "C" void paco_plan_destroy(paco_plan_t *pl)
 {
     if (!pl) return;
     batched_destroy(pl->bs);
+    cudaFree(pl->tc);
     cudaFree(pl->twL1);
     cudaFree(pl->twL2);
     cudaFree(pl->twN_lo);
@@ -467,6 +486,7 @@ static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int m
     a.twN_hi = pl->twN_hi;
     a.twN_lo_bits = pl->twN_lo_bits;
     a.pad = (mode == 1) ? 1 : (1 << sc.lgW);
+    a.tc = pl->tc;
     if (mode == 1 || mode == 3) {         // over the input view: L = N1, C = N2
         a.C = (int)pl->N2;
         a.twL = pl->twL1;

@@ -188,6 +188,7 @@ struct StageArgs {
     unsigned N_mask;        // N - 1
     int conj;               // 1: conjugate on load and store (dir = +1)
     int pad;                // shared-memory row padding (elements)
+    const void *tc;         // tensor-core forms: fragment table (paco_tc.cuh)
 };
 
 } // namespace paco

@@ -41,6 +41,8 @@ struct paco_plan {
     unsigned *ctr = nullptr;       // panel pipeline counters
     size_t ctr_words = 0;
     int num_sms = 0;
+    int form = 0;                  // tensor-core precision form (paco_tc.cuh), 0 = plain
+    void *tc = nullptr;            // its fragment table
     // uneven batch (paco_plan_create_batched): N = total elements, batch = 1
     paco::BatchedState *bs = nullptr;
 };
@@ -52,6 +54,10 @@ int ilog2_exact(int64_t v);
 // FP64-generated table of w_M^{-(r*mult)}, r in [count], complex of `esize` bytes
 paco_status_t gen_table(int esize, void **dst, long long M, long long count, long long mult,
                         cudaStream_t stream);
+
+// paco_stage_tc.cu
+const void *stage_kernel_fn_tc(int lgL, int form);
+paco_status_t tc_table_create(int form, void **out);
 
 // paco_permute.cu
 paco_status_t launch_permute(const paco_plan *pl, const void *A_tilde, void *W, int dir,

@@ -39,6 +39,7 @@
 #include <cooperative_groups.h>
 
 #include "paco_common.cuh"
+#include "paco_tc.cuh"
 
 namespace paco {
 
@@ -104,7 +105,10 @@ __host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int 
 // cluster rank `rank`) computed by the calling CTA's NT = NE / EPT threads.
 // LDCG loads the tile input through L2 only (ld.global.cg): for inputs that
 // other CTAs of the same launch wrote (the batched persistent kernel).
-template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG>
+// FORM != TC_NONE computes the radix-16 passes (F1 and F2 pass 1 when the
+// radix is 16) as tensor-core contractions (paco_tc.cuh); its fragment table
+// and per-warp staging follow the stage's shared memory.
+template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE>
 __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long long boff, int rank,
                                            unsigned char *smem_raw)
 {
@@ -141,6 +145,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     C *thi = tlo + SL;            // w_L^{-r*SL}, r < SH
     C *E1 = thi + SH;             // mode 1: w_N^{-k_lo c}     [Ak][W]
     C *E2 = E1 + Ak * W;          // mode 1: w_N^{-A k_hi c}   [B][W]
+    const uint4 *tc_tab = nullptr;
+    uint32_t *tc_ws = nullptr;
+    if constexpr (FORM != TC_NONE) {
+        static_assert(sizeof(R) == 4, "tensor-core forms are complex64");
+        const int elems = data_elems + A + B + SL + SH + Ak * W + B * W;
+        unsigned char *base = smem_raw + (((size_t)elems * sizeof(C) + 15) & ~(size_t)15);
+        tc_tab = reinterpret_cast<const uint4 *>(base);
+        tc_ws = reinterpret_cast<uint32_t *>(base + TcForm<FORM>::TABLE_U4 * 16) +
+                (threadIdx.x >> 5) * TcForm<FORM>::WARP_WORDS;
+        const uint4 *src = reinterpret_cast<const uint4 *>(args.tc);
+        uint4 *dst = reinterpret_cast<uint4 *>(base);
+        for (int r = threadIdx.x; r < TcForm<FORM>::TABLE_U4; r += blockDim.x) dst[r] = src[r];
+    }
 
     const int tid = threadIdx.x;
     const int c0 = tile << lgW;
@@ -198,7 +215,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                 x.y *= csign;
                 v[u * RA1 + r] = x;
             }
-            dft<RA1>(v + u * RA1);
+            if constexpr (FORM != TC_NONE && RA1 == 16) tc_dft16<FORM>(v + u * RA1, tc_tab, tc_ws);
+            else dft<RA1>(v + u * RA1);
             if constexpr (RA2 > 1) {
 #pragma unroll
                 for (int s = 1; s < RA1; ++s)
@@ -287,7 +305,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
         const int al = (bfi >> lgW) / RB2;
 #pragma unroll
         for (int r = 0; r < RB1; ++r) v[u * RB1 + r] = sm[al * P2 + ((jj + RB2 * r) << lgW) + col];
-        dft<RB1>(v + u * RB1);
+        if constexpr (FORM != TC_NONE && RB1 == 16) tc_dft16<FORM>(v + u * RB1, tc_tab, tc_ws);
+        else dft<RB1>(v + u * RB1);
         if constexpr (RB2 > 1) {
 #pragma unroll
             for (int s = 1; s < RB1; ++s) v[u * RB1 + s] = cmul(v[u * RB1 + s], twB[s * jj]);
@@ -348,15 +367,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     }
 }
 
-template <typename R, int A, int B, int LGWC = -1, int LGKC = -1, int MC = 0, int MINB = 1>
+template <typename R, int A, int B, int LGWC = -1, int LGKC = -1, int MC = 0, int MINB = 1, int FORM = TC_NONE>
 __global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lgK = (LGKC >= 0) ? LGKC : args.lgK;
     int rank = 0;
     if ((1 << lgK) > 1) rank = (int)cg::this_cluster().block_rank();
-    stage_tile<R, A, B, LGWC, LGKC, MC, false>(args, (int)(blockIdx.x >> lgK),
-                                               (long long)blockIdx.y * args.batch_stride, rank, smem_raw);
+    stage_tile<R, A, B, LGWC, LGKC, MC, false, FORM>(args, (int)(blockIdx.x >> lgK),
+                                                     (long long)blockIdx.y * args.batch_stride, rank, smem_raw);
 }
 
 // L = A (B == 1): the whole transform is F1; store straight from F1's layout.

@@ -98,3 +98,11 @@ def test_batched_plan_rejects_bad_arguments():
     o = paco.BatchedOpts(0, 3, 1, 0)                                             # radix 3
     assert L.paco_plan_create_batched_ex(ctypes.byref(h), arr, 2, paco.C64, ctypes.byref(o)) == 1
     assert L.paco_plan_batched_config(None, 256, None, None, None, None) == 1
+
+
+@pytest.mark.parametrize("dtype_name", ["C64_TC_BF16X3", "C64_TC_FP16"])
+def test_tc_forms_reject_small_factors(dtype_name):
+    import paper_2609_06449_gb300 as paco
+    with pytest.raises(paco.PacoError) as ei:
+        paco.Plan(128, 256, 2, 1, getattr(paco, dtype_name))
+    assert ei.value.status == 2 and "2^8" in str(ei.value)

@@ -1,0 +1,76 @@
+"""GPU parity of the tensor-core precision forms: radix-16 sub-DFTs as
+BF16 3-term split or FP16 per-block-scaled contractions with FP32
+accumulation, against the FP64 oracle.  Bounds: the BF16x3 form must meet
+the complex64 bound 5e-7*log2(N); the FP16 form the FP16 bound 1e-3
+(relative L2 per transform)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paco_inputs import loguniform, uniform
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2609_06449_gb300 as paco  # noqa: E402
+
+FORMS = {"bf16x3": paco.C64_TC_BF16X3, "fp16": paco.C64_TC_FP16}
+
+
+def bound(form, N):
+    return 5e-7 * math.log2(N) if form == "bf16x3" else 1e-3
+
+
+def rel_l2(got, ref):
+    got = np.asarray(got, dtype=np.complex128).reshape(ref.shape)
+    return float(np.max(np.linalg.norm(got - ref, axis=-1) / np.linalg.norm(ref, axis=-1)))
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+@pytest.mark.parametrize("N1,N2,b,batch", [(256, 256, 4, 3), (256, 256, 2, 1), (1024, 256, 4, 2),
+                                           (256, 4096, 16, 1), (4096, 4096, 4, 2)])
+@pytest.mark.parametrize("gen", ["uniform", "loguniform"])
+def test_tc_form_vs_oracle(form, N1, N2, b, batch, gen):
+    N = N1 * N2
+    mk = uniform if gen == "uniform" else loguniform
+    x = mk(batch * N, N1 + N2 + batch, np.complex64).reshape(batch, N)
+    plan = paco.Plan(N1, N2, b, batch, FORMS[form])
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+    for d in (-1, 1):
+        plan.execute(xt, out, d)
+        torch.cuda.synchronize()
+        plan.check()
+        ref = oracle.fft(x.astype(np.complex128), dir=d)
+        err = rel_l2(out.cpu().numpy(), ref)
+        assert err <= bound(form, N), f"{form} dir={d} rel_l2={err:.3e}"
+
+
+@pytest.mark.parametrize("form", list(FORMS))
+def test_tc_form_full_size_sampled(form):
+    """N = 2^28 (2^14 x 2^14, b = 4): sampled outputs against the oracle's
+    single-coefficient DFT, plus Parseval over the whole transform."""
+    N1 = N2 = 2 ** 14
+    N = N1 * N2
+    plan = paco.Plan(N1, N2, 4, 1, FORMS[form], p=64)
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.view_as_complex(torch.rand(N, 2, generator=g, device="cuda") * 2 - 1)
+    y = torch.empty_like(x)
+    plan.execute(x, y, -1)
+    torch.cuda.synchronize()
+    plan.check()
+    ex = (x.abs().double() ** 2).sum().item()
+    ey = (y.abs().double() ** 2).sum().item()
+    assert abs(ey / (N * ex) - 1) <= (1e-5 if form == "bf16x3" else 2e-3)
+    ks = np.random.default_rng(3).integers(0, N, 48)
+    xh = x.cpu().numpy()
+    ref = oracle.dft_at(xh.astype(np.complex128), ks)
+    got = y.cpu().numpy()[ks]
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= bound(form, N), err
