@@ -107,22 +107,38 @@ __device__ __forceinline__ void small_group(const BatchedArgs &a, const BLen &ld
     constexpr int HM = (N1 < 32 ? N1 : 32) - 1;                 // swizzle mask
     const int tid = threadIdx.x;
     const int t = ld.t;
-    const C *tw = reinterpret_cast<const C *>(ld.twN);
     const bool cj = a.conj != 0;
+    // w_N^{-r} = lo[r mod 2^LH] * hi[r >> LH], both halves in shared memory
+    constexpr int LH = (LGN + 1) / 2;
+    C *tw_lo = reinterpret_cast<C *>(s_off + G);
+    C *tw_hi = tw_lo + (1 << LH);
+    {
+        const C *tw = reinterpret_cast<const C *>(ld.twN);
+        for (int r = tid; r < (1 << LH); r += batched::NT) tw_lo[r] = tw[r];
+        for (int r = tid; r < (N >> LH); r += batched::NT) tw_hi[r] = tw[r << LH];
+    }
+    auto twid = [&](int r) { return cmul(tw_lo[r & ((1 << LH) - 1)], tw_hi[r >> LH]); };
 
     for (int g = tid; g < gcount; g += batched::NT) s_off[g] = a.off[a.group_tx[gstart + g]];
     __syncthreads();
-    // load: 16-byte vectors, conjugated for dir = +1
+    // load: 16-byte vectors, all issued before any use, conjugated for dir = +1
     {
+        constexpr int NV = batched::ITEM / 2 / batched::NT;
         const float4 *src = reinterpret_cast<const float4 *>(a.in);
-        for (int e = tid; e < G * N / 2; e += batched::NT) {
+        float4 r4[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int e = tid + batched::NT * i;
             const int g = (2 * e) >> LGN, r = (2 * e) & (N - 1);
-            if (g < gcount) {
-                float4 v = __ldg(src + ((s_off[g] + r) >> 1));
-                if (cj) { v.y = -v.y; v.w = -v.w; }
-                S[2 * e] = make_cx<float>(v.x, v.y);
-                S[2 * e + 1] = make_cx<float>(v.z, v.w);
-            }
+            r4[i] = (g < gcount) ? __ldg(src + ((s_off[g] + r) >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const int e = tid + batched::NT * i;
+            float4 v4 = r4[i];
+            if (cj) { v4.y = -v4.y; v4.w = -v4.w; }
+            S[2 * e] = make_cx<float>(v4.x, v4.y);
+            S[2 * e + 1] = make_cx<float>(v4.z, v4.w);
         }
     }
     __syncthreads();
@@ -143,7 +159,7 @@ __device__ __forceinline__ void small_group(const BatchedArgs &a, const BLen &ld
         dft<R1>(v + q * R1);
         if constexpr (R2 > 1) {
 #pragma unroll
-            for (int s = 1; s < R1; ++s) v[q * R1 + s] = cmul(v[q * R1 + s], tw[s * jl * N2]);
+            for (int s = 1; s < R1; ++s) v[q * R1 + s] = cmul(v[q * R1 + s], twid(s * jl * N2));
 #pragma unroll
             for (int s = 0; s < R1; ++s) base[s * R2 * N2] = v[q * R1 + s];
         }
@@ -182,7 +198,7 @@ __device__ __forceinline__ void small_group(const BatchedArgs &a, const BLen &ld
 #pragma unroll
             for (int k = 0; k < RF; ++k) {
                 const int k1 = (R2 > 1) ? (kl + R1 * k) : k;
-                row[k1 ^ h] = cmul(v[q * RF + k], tw[k1 * c]);
+                row[k1 ^ h] = cmul(v[q * RF + k], twid(k1 * c));
             }
         }
     }
@@ -209,7 +225,7 @@ __device__ __forceinline__ void small_group(const BatchedArgs &a, const BLen &ld
         if constexpr (Q2 > 1) {
 #pragma unroll
             for (int s = 0; s < Q1; ++s) {
-                C y = (s > 0) ? cmul(v[q * Q1 + s], tw[s * jl * N1]) : v[q * Q1 + s];
+                C y = (s > 0) ? cmul(v[q * Q1 + s], twid(s * jl * N1)) : v[q * Q1 + s];
                 const int j = s * Q2 + jl;
                 const int row = (int)digit_reverse((unsigned)j, LG2, t);
                 base[row * N1 + (col ^ (j & HM))] = y;
@@ -307,9 +323,15 @@ __global__ void __launch_bounds__(batched::NT, MINB) paco_batched_kernel(const _
     __shared__ int s_ok;
     __shared__ StageArgs s_sa;
     const int tid = threadIdx.x;
+    // the next item is claimed while the current one runs
+    unsigned next = 0;
+    if (tid == 0) next = atomicAdd(&a.ctr[0], 1u);
     for (;;) {
         __syncthreads();                          // the previous item is done with shared memory
-        if (tid == 0) s_item = (int)atomicAdd(&a.ctr[0], 1u);
+        if (tid == 0) {
+            s_item = (int)next;
+            if ((int)next < a.nitems) next = atomicAdd(&a.ctr[0], 1u);
+        }
         __syncthreads();
         const int it = s_item;
         if (it >= a.nitems) break;
@@ -450,7 +472,7 @@ static paco_status_t build_device(paco_plan *pl, BatchedState *bs)
     int nsm = pl->num_sms;
     const void *fn = batched_fn(bs->minb);
     // shared memory: the largest stage tile or a small group
-    int smem = batched::ITEM * 8 + (batched::ITEM / 16) * 8;
+    int smem = batched::ITEM * 8 + (batched::ITEM / 16) * 8 + (128 + 64) * 8;
     for (int lg : bs->lgs) {
         const LenCfg &c = bs->cfg[lg];
         if (lg <= batched::SMALL_MAX_LG) continue;

@@ -300,9 +300,19 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
 #pragma unroll
     for (int u = 0; u < NB1; ++u) {
         const int bfi = tid + NT * u;
-        const int col = bfi & (W - 1);
-        const int jj = (bfi >> lgW) % RB2;
-        const int al = (bfi >> lgW) / RB2;
+        int col, jj, al;
+        if (RB2 == 1 && mode == 1) {
+            // single F2 pass in Phase I: k_lo fastest across threads, so the
+            // stores below write runs of consecutive k1 of one W row (the row
+            // pitch P2 is odd in mode 1: conflict-free shared-memory reads)
+            al = bfi & (Ak - 1);
+            col = (bfi >> (ilog2c<A>::value - lgK)) & (W - 1);
+            jj = 0;
+        } else {
+            col = bfi & (W - 1);
+            jj = (bfi >> lgW) % RB2;
+            al = (bfi >> lgW) / RB2;
+        }
 #pragma unroll
         for (int r = 0; r < RB1; ++r) v[u * RB1 + r] = sm[al * P2 + ((jj + RB2 * r) << lgW) + col];
         if constexpr (FORM != TC_NONE && RB1 == 16) tc_dft16<FORM>(v + u * RB1, tc_tab, tc_ws);
@@ -338,9 +348,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             dft<RB2>(v + u * RB2);
         } else {
             // single F2 pass: the registers already hold the outputs of
-            // butterfly (col, jj = 0, al)
-            col = bfi & (W - 1);
-            al = bfi >> lgW;
+            // butterfly (col, jj = 0, al), mapped as in F2 pass 1
+            if (mode == 1) {
+                al = bfi & (Ak - 1);
+                col = (bfi >> (ilog2c<A>::value - lgK)) & (W - 1);
+            } else {
+                col = bfi & (W - 1);
+                al = bfi >> lgW;
+            }
             hi = 0;
         }
         const int klo = rank * Ak + al;
