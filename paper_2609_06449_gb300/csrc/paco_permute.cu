@@ -49,15 +49,28 @@ __global__ void __launch_bounds__(256) paco_permute_kernel(const PermuteArgs a)
         const C *src = reinterpret_cast<const C *>(a.in) + bt * a.N;
         C *dst = reinterpret_cast<C *>(a.out) + bt * a.N;
         if (tx < TC) {
+            // all loads of the thread first (4 rows of the tile), then the twiddles
             const unsigned c = (unsigned)(c0 + tx);
-            for (int i = ty; i < TV; i += 8) {
-                const unsigned v = (unsigned)(v0 + i);
-                const unsigned arow = digit_reverse(v, a.bits1, a.t);     // a = pi_m1(v)
-                C x = src[(long long)arow * a.N2 + c];
-                const unsigned r = (v * c) & a.N_mask;
-                C w = cmul(lo[r & lomask], hi[r >> a.twN_lo_bits]);       // w_N^{-vc}
-                if (a.conj) w.y = -w.y;
-                tile[i][tx] = cmul(x, w);
+            C x[4], w[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = ty + 8 * q;
+                if (i < TV) {
+                    const unsigned v = (unsigned)(v0 + i);
+                    const unsigned arow = digit_reverse(v, a.bits1, a.t);     // a = pi_m1(v)
+                    const unsigned r = (v * c) & a.N_mask;
+                    x[q] = src[(long long)arow * a.N2 + c];
+                    w[q] = cmul(lo[r & lomask], hi[r >> a.twN_lo_bits]);      // w_N^{-vc}
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = ty + 8 * q;
+                if (i < TV) {
+                    C wq = w[q];
+                    if (a.conj) wq.y = -wq.y;
+                    tile[i][tx] = cmul(x[q], wq);
+                }
             }
         }
         __syncthreads();

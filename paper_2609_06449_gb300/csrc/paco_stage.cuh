@@ -143,7 +143,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     C *twB = twA + A;             // w_B^{-r}, r < B
     C *tlo = twB + B;             // w_L^{-r}, r < SL
     C *thi = tlo + SL;            // w_L^{-r*SL}, r < SH
-    C *E1 = thi + SH;             // mode 1: w_N^{-k_lo c}     [Ak][W]
+    C *E1 = thi + SH;             // mode 1: w_N^{-k_lo c}     [W][Ak]
     C *E2 = E1 + Ak * W;          // mode 1: w_N^{-A k_hi c}   [B][W]
     const uint4 *tc_tab = nullptr;
     uint32_t *tc_ws = nullptr;
@@ -178,8 +178,10 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             for (int e = tid; e < nE; e += NT) {
                 unsigned r;
                 if (e < nE1) {
-                    const unsigned klo = (unsigned)(rank * Ak + (e >> lgW));
-                    const unsigned c = (unsigned)(c0 + (e & (W - 1)));
+                    // E1 is [col][k_lo]: the epilogue reads it with k_lo fastest
+                    const int lgAk = ilog2c<A>::value - lgK;
+                    const unsigned klo = (unsigned)(rank * Ak + (e & (Ak - 1)));
+                    const unsigned c = (unsigned)(c0 + (e >> lgAk));
                     r = (klo * c) & args.N_mask;
                 } else {
                     const int e2 = e - nE1;
@@ -367,7 +369,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             C y = v[u * RL + k];
             long long idx;
             if (mode == 1) {
-                y = cmul(y, cmul(E1[(al << lgW) + col], E2[(khi << lgW) + col]));
+                y = cmul(y, cmul(E1[(col << (ilog2c<A>::value - lgK)) + al], E2[(khi << lgW) + col]));
                 const unsigned urow = digit_reverse((unsigned)c, args.rev_bits, args.rev_t);
                 idx = (long long)urow * args.out_ld + kk;
             } else if (mode == 2) {
