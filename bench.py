@@ -20,7 +20,9 @@ sample, and SM clocks sampled during the timed region.
 Other workloads (--workload): A (2^16 as 256 x 256, latency), B128
 (complex128 N = 2^27), C (the uneven batch in one persistent launch), D
 (16 x 2^24 per precision form), E (forward + backward of 256 x 2^20 through
-the autograd function).  Each prints one line of the same contract.
+the autograd function), U (the unfused three-pass pipeline Phase I ->
+paco_permute -> Phase III on the headline transform: the ablation of the
+fused redistribution).  Each prints one line of the same contract.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paco|reference]
                   [--workload B|A|B128|C|D|E]
@@ -66,7 +68,13 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["B", "A", "B128", "C", "D", "E"], default="B")
+    ap.add_argument("--workload", choices=["B", "A", "B128", "C", "D", "E", "U"], default="B")
+    ap.add_argument("--small", action="store_true",
+                    help="a reduced case of the workload (C: 1024 lengths to 2^26 + 4096 x 2^12; D: batch 2; "
+                         "U: N = 2^26), for ncu captures")
+    ap.add_argument("--no-autotune", action="store_true", help="C: fixed configuration instead of autotuning")
+    ap.add_argument("--form", choices=["all", "plain", "bf16x3", "fp16"], default="all",
+                    help="D: time only this precision form")
     ap.add_argument("--no-tc", action="store_true", help="skip the tensor-core forms on the headline line")
     return ap.parse_args()
 
@@ -506,11 +514,15 @@ def run_other(args, ranks, local):
                               "traffic": None, "hbm": hr},
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, "c128"), gpu_launches=2 * K, clocks=clocks)
     elif wl == "C":
-        e = uneven_lengths()
-        lengths = np.concatenate([2 ** e, np.full(2 ** 14, 2 ** 12)]).astype(np.int64)
+        if args.small:
+            e = uneven_lengths(count=1024, seed=0, lo=8, hi=20, total_log2=26)
+            lengths = np.concatenate([2 ** e, np.full(2 ** 12, 2 ** 12)]).astype(np.int64)
+        else:
+            e = uneven_lengths()
+            lengths = np.concatenate([2 ** e, np.full(2 ** 14, 2 ** 12)]).astype(np.int64)
         total = int(lengths.sum())
         t_plan = time.time()
-        plan = paco.BatchedPlan(lengths)
+        plan = paco.BatchedPlan(lengths, autotune=not args.no_autotune, ctas_per_sm=2, lag=2)
         t_plan = time.time() - t_plan
         xh = torch.from_numpy(gaussian(total, rank, np.complex64)).pin_memory()
         x = xh.cuda()
@@ -540,7 +552,7 @@ def run_other(args, ranks, local):
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=18), gpu_launches=K, clocks=clocks)
     elif wl == "D":
         N1 = N2 = 4096
-        N, B = N1 * N2, 16
+        N, B = N1 * N2, (2 if args.small else 16)
         xh = torch.from_numpy(np.concatenate([
             __import__("paco_inputs").loguniform(N, 100 * rank + i, np.complex64) for i in range(B)])).pin_memory()
         x = xh.cuda()
@@ -549,6 +561,8 @@ def run_other(args, ranks, local):
         forms = {}
         clocks = None
         for name, dt in (("plain", paco.C64), ("bf16x3", paco.C64_TC_BF16X3), ("fp16", paco.C64_TC_FP16)):
+            if args.form not in ("all", name):
+                continue
             pl = paco.Plan(N1, N2, 4, B, dt)
             for _ in range(W):
                 pl.execute(x, y, -1, stream)
@@ -562,22 +576,69 @@ def run_other(args, ranks, local):
             if name == "bf16x3":
                 clocks = ck
             pl.close()
-        line = dict(base, value=forms["bf16x3"]["value"], unit="GFLOP/s", higher_is_better=True,
-                    ms_per_step=forms["bf16x3"]["ms_per_step"], dtype="bf16x3 operands, f32 accumulate",
-                    config={"workload": "16 x c64 1-D DFT N=2^24 (4096 x 4096, b=4), forward; precision forms",
+        head = "bf16x3" if "bf16x3" in forms else next(iter(forms))
+        hdt = {"plain": paco.C64, "bf16x3": paco.C64_TC_BF16X3, "fp16": paco.C64_TC_FP16}[head]
+        clocks = clocks or ck
+        line = dict(base, value=forms[head]["value"], unit="GFLOP/s", higher_is_better=True,
+                    ms_per_step=forms[head]["ms_per_step"],
+                    dtype={"plain": "f32", "bf16x3": "bf16x3 operands, f32 accumulate",
+                           "fp16": "f16 operands (per-block scaled), f32 accumulate"}[head],
+                    config={"workload": f"{B} x c64 1-D DFT N=2^24 (4096 x 4096, b=4), forward; precision forms",
+                            "form_of_value": head,
                             "input": "log-uniform magnitudes 1e-4..1e4, uniform phases, seed = 100*rank + i",
                             "l2": "inputs larger than L2"},
                     forms=forms,
-                    roofline=hbm_roofline("TC stage kernel (bf16x3)", 16.0 * N * B,
-                                          forms["bf16x3"]["dominant_launch_ms"]),
-                    e2e=None, cpu_baseline=cpu_leg(args, rank, world), gpu_launches=2 * K * 3, clocks=clocks)
-        # e2e for the headline form of this line
-        pl = paco.Plan(N1, N2, 4, B, paco.C64_TC_BF16X3)
+                    roofline=hbm_roofline(f"stage kernel ({head})", 16.0 * N * B,
+                                          forms[head]["dominant_launch_ms"]),
+                    e2e=None, cpu_baseline=cpu_leg(args, rank, world), gpu_launches=2 * K * len(forms), clocks=clocks)
+        # e2e for the form of the line's value
+        pl = paco.Plan(N1, N2, 4, B, hdt)
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
         line["e2e"] = e2e_host(lambda: pl.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1),
                                stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
                                "paco_execute_host (pinned host buffers)", mor, world, ranks.barrier)
+    elif wl == "U":
+        lg = 13 if args.small else 14
+        N1 = N2 = 1 << lg
+        N = N1 * N2
+        plan = paco.Plan(N1, N2, 4 if lg % 2 == 0 else 2, 1, paco.C64, p=64 if lg % 2 == 0 else 32)
+        xh = torch.from_numpy(uniform(N, rank, np.complex64)).pin_memory()
+        x = xh.cuda()
+        at = torch.empty_like(x)
+        w = torch.empty_like(x)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+
+        def step3(k=[0]):
+            i = k[0] % K
+            ev[i][0].record(stream)
+            plan.execute_phase1(x, at, -1, stream)
+            ev[i][1].record(stream)
+            plan.permute(at, w, -1, stream)
+            ev[i][2].record(stream)
+            plan.execute_stage2(w, w, -1, stream)
+            ev[i][3].record(stream)
+            k[0] += 1
+        for _ in range(W):
+            step3()
+        tot, per, clocks = timed(step3)
+        plan.check()
+        sp = [statistics.mean(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(K)) for j in range(3)]
+        flop = 5.0 * N * 2 * lg
+        ms = mor(tot) / K
+        # the fused two-pass path on the same transform, for the ratio
+        yf = torch.empty_like(x)
+        ftot, fper = time_steps(lambda: plan.execute(x, yf, -1, stream), K, 3, stream)
+        line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s", higher_is_better=True,
+                    ms_per_step=ms, dtype="f32",
+                    config={"workload": f"c64 1-D DFT N=2^{2 * lg} unfused: Phase I -> paco_permute -> Phase III",
+                            "N1": N1, "N2": N2, "input": "Re, Im i.i.d. U[-1,1), seed = rank",
+                            "l2": "inputs larger than L2"},
+                    pass_ms={"phase1": sp[0], "permute": sp[1], "phase3": sp[2]},
+                    fused_ms_per_step=mor(ftot) / K,
+                    hbm_gbs_effective=48.0 * N * world / (ms * 1e-3) / 1e9,
+                    roofline=hbm_roofline("paco_permute_kernel", 16.0 * N, sp[1]),
+                    e2e=None, cpu_baseline=cpu_leg(args, rank, world), gpu_launches=3 * K, clocks=clocks)
     else:  # E
         N1 = N2 = 1024
         N, B = N1 * N2, 256

@@ -82,6 +82,8 @@ typedef struct {
     paco_dtype_t dtype;
     int tile_w;          /* columns per tile; 0 = default */
     int cluster;         /* CTAs per cluster (1, 2, 4, 8); 0 = default */
+    int ctas_per_sm;     /* resident CTAs per SM the stage kernels are compiled
+                            for (1 or 2; complex64 stage kernels only); 0 = default */
 } paco_plan_opts_t;
 
 /* Read-only description of a plan (paco_plan_info). */

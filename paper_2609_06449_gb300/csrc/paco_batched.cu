@@ -60,11 +60,13 @@ struct BLen {
     StageArgs s1, s2;              // stage: mode 1 and mode 2 (in/out/conj set per item)
 };
 
-struct BItem {
+struct __align__(16) BItem {
     int kind;                      // 0 small group, 1 Phase I tile, 2 Phase III tile
     int len;                       // index into the length table
     int a;                         // kind 0: first entry of group_tx; else transform index
     int b;                         // kind 0: transforms in the group; else tile index
+    long long off;                 // stage tiles: element offset of the transform
+    long long pad;
 };
 
 struct BatchedArgs {
@@ -278,10 +280,12 @@ __device__ __noinline__ void small_item(const BatchedArgs &a, const BLen &ld, in
     small_group<LG1, LG2>(a, ld, gs, gc, S, so);
 }
 
-template <int A, int B>
+// LDCG: Phase III reads W, written by other CTAs of this launch, through L2
+// only; Phase I reads the launch's read-only input through the read-only path.
+template <int A, int B, bool LDCG>
 __device__ __noinline__ void stage_item(const StageArgs &sa, int tile, long long boff, unsigned char *smem)
 {
-    stage_tile<float, A, B, -1, 0, 0, true>(sa, tile, boff, 0, smem);
+    stage_tile<float, A, B, -1, 0, 0, LDCG>(sa, tile, boff, 0, smem);
 }
 
 __device__ __forceinline__ void small_dispatch(const BatchedArgs &a, const BLen &ld, int gs, int gc,
@@ -302,15 +306,16 @@ __device__ __forceinline__ void small_dispatch(const BatchedArgs &a, const BLen 
     }
 }
 
+template <bool LDCG>
 __device__ __forceinline__ void stage_dispatch(const StageArgs &sa, int lgL, int tile, long long boff,
                                                unsigned char *smem)
 {
     switch (lgL) {
-    case 6: stage_item<8, 8>(sa, tile, boff, smem); break;
-    case 7: stage_item<16, 8>(sa, tile, boff, smem); break;
-    case 8: stage_item<16, 16>(sa, tile, boff, smem); break;
-    case 9: stage_item<32, 16>(sa, tile, boff, smem); break;
-    case 10: stage_item<32, 32>(sa, tile, boff, smem); break;
+    case 6: stage_item<8, 8, LDCG>(sa, tile, boff, smem); break;
+    case 7: stage_item<16, 8, LDCG>(sa, tile, boff, smem); break;
+    case 8: stage_item<16, 16, LDCG>(sa, tile, boff, smem); break;
+    case 9: stage_item<32, 16, LDCG>(sa, tile, boff, smem); break;
+    case 10: stage_item<32, 32, LDCG>(sa, tile, boff, smem); break;
     default: break;
     }
 }
@@ -319,23 +324,40 @@ template <int MINB>
 __global__ void __launch_bounds__(batched::NT, MINB) paco_batched_kernel(const __grid_constant__ BatchedArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_item;
+    __shared__ BItem s_it;
     __shared__ int s_ok;
+    __shared__ int s_key;                         // (length, kind) whose descriptor s_sa holds
     __shared__ StageArgs s_sa;
     const int tid = threadIdx.x;
-    // the next item is claimed while the current one runs
-    unsigned next = 0;
-    if (tid == 0) next = atomicAdd(&a.ctr[0], 1u);
+    // Thread 0 keeps the next item (claimed and loaded) and the index of the
+    // one after it (claimed) in registers: both round trips overlap the
+    // current item.  Claiming ahead cannot deadlock: the lowest-indexed
+    // claimed, unfinished item is always some CTA's current item, and it only
+    // waits on lower-indexed items, which are all finished.
+    BItem nit;
+    int nidx = 0, nidx2 = 0;
+    if (tid == 0) {
+        s_key = -1;
+        nidx = (int)atomicAdd(&a.ctr[0], 1u);
+        nidx2 = (int)atomicAdd(&a.ctr[0], 1u);
+        if (nidx < a.nitems) nit = a.items[nidx];
+        else nit.kind = -1;
+    }
     for (;;) {
         __syncthreads();                          // the previous item is done with shared memory
         if (tid == 0) {
-            s_item = (int)next;
-            if ((int)next < a.nitems) next = atomicAdd(&a.ctr[0], 1u);
+            s_it = nit;
+            nidx = nidx2;
+            if (nidx < a.nitems) {
+                nit = a.items[nidx];
+                nidx2 = (int)atomicAdd(&a.ctr[0], 1u);
+            } else {
+                nit.kind = -1;
+            }
         }
         __syncthreads();
-        const int it = s_item;
-        if (it >= a.nitems) break;
-        const BItem item = a.items[it];
+        const BItem item = s_it;
+        if (item.kind < 0) break;
         const BLen &ld = a.lens[item.len];
         if (item.kind == 0) {
             cx<float> *S = reinterpret_cast<cx<float> *>(smem_raw);
@@ -343,14 +365,16 @@ __global__ void __launch_bounds__(batched::NT, MINB) paco_batched_kernel(const _
             small_dispatch(a, ld, item.a, item.b, S, so);
             continue;
         }
-        if (tid == 0) {
+        const int key = item.len * 4 + item.kind;
+        if (tid == 0 && s_key != key) {
             s_sa = (item.kind == 1) ? ld.s1 : ld.s2;
             s_sa.in = (item.kind == 1) ? a.in : a.out;
             s_sa.out = a.out;
             s_sa.conj = a.conj;
+            s_key = key;
         }
         const StageArgs &sa = s_sa;
-        const long long boff = a.off[item.a];
+        const long long boff = item.off;
         if (item.kind == 2) {
             if (tid == 0) {
                 const unsigned need = (unsigned)ld.ntiles1;
@@ -366,10 +390,10 @@ __global__ void __launch_bounds__(batched::NT, MINB) paco_batched_kernel(const _
             }
             __syncthreads();
             if (!s_ok) continue;                  // reported through the status word
-            stage_dispatch(sa, ld.lg2, item.b, boff, smem_raw);
+            stage_dispatch<true>(sa, ld.lg2, item.b, boff, smem_raw);
         } else {
             __syncthreads();                      // s_sa written
-            stage_dispatch(sa, ld.lg1, item.b, boff, smem_raw);
+            stage_dispatch<false>(sa, ld.lg1, item.b, boff, smem_raw);
             __syncthreads();                      // every store of the tile issued
             if (tid == 0) {
                 __threadfence();
@@ -563,6 +587,7 @@ static paco_status_t build_device(paco_plan *pl, BatchedState *bs)
         if (lg > batched::SMALL_MAX_LG) { big.push_back(i); ++k; continue; }
         const int G = batched::ITEM >> lg;
         BItem it;
+        memset(&it, 0, sizeof(it));
         it.kind = 0;
         it.len = len_index[lg];
         it.a = (int)group.size();
@@ -581,11 +606,11 @@ static paco_status_t build_device(paco_plan *pl, BatchedState *bs)
     std::deque<std::pair<int, long long>> pending;  // (transform, earliest position)
     auto emit_s2 = [&](int tr) {
         const BLen &L = lens[(size_t)len_index[ilog2_exact(bs->lengths[(size_t)tr])]];
-        for (int tl = 0; tl < L.ntiles2; ++tl) items.push_back(BItem{2, len_index[L.lgN], tr, tl});
+        for (int tl = 0; tl < L.ntiles2; ++tl) items.push_back(BItem{2, len_index[L.lgN], tr, tl, bs->off[(size_t)tr], 0});
     };
     for (int tr : big) {
         const int li = len_index[ilog2_exact(bs->lengths[(size_t)tr])];
-        for (int tl = 0; tl < lens[(size_t)li].ntiles1; ++tl) items.push_back(BItem{1, li, tr, tl});
+        for (int tl = 0; tl < lens[(size_t)li].ntiles1; ++tl) items.push_back(BItem{1, li, tr, tl, bs->off[(size_t)tr], 0});
         pending.emplace_back(tr, (long long)items.size() + lag);
         while (!pending.empty() && pending.front().second <= (long long)items.size()) {
             emit_s2(pending.front().first);

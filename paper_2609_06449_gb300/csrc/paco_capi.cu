@@ -23,8 +23,8 @@
 #include "paco_stage.cuh"
 
 namespace paco {
-const void *stage_kernel_fn_f32(int lgL);
-const void *stage_kernel_fn_f64(int lgL);
+const void *stage_kernel_fn_f32(int lgL, int minb);
+const void *stage_kernel_fn_f64(int lgL, int minb);
 const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
 const void *panel_kernel_fn();
@@ -126,6 +126,7 @@ static void choose_tile(const paco_plan *pl, int lgL, int64_t C, int req_w, int 
 }
 
 static const int kPanelWidth = 128;
+static const bool kDefaultTwoCtas = true;
 
 static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode,
                                  int req_w, int req_k)
@@ -158,7 +159,7 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
     } else {
         sc->fn = (pl->esize == 8) ? stage_kernel_fn_special_f32(lgL, sc->lgW, sc->lgK, mode)
                                   : stage_kernel_fn_special_f64(lgL, sc->lgW, sc->lgK, mode);
-        if (!sc->fn) sc->fn = (pl->esize == 8) ? stage_kernel_fn_f32(lgL) : stage_kernel_fn_f64(lgL);
+        if (!sc->fn) sc->fn = (pl->esize == 8) ? stage_kernel_fn_f32(lgL, 1) : stage_kernel_fn_f64(lgL, 1);
     }
     if (!sc->fn) return fail(PACO_ERR_UNSUPPORTED, "stage length 2^%d is not built (max 2^14)", lgL);
     if (B == 1) {
@@ -176,6 +177,13 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
                     (long long)NE, sc->threads);
     if (sc->smem > 227 * 1024)
         return fail(PACO_ERR_INVALID_ARG, "tile needs %d bytes of shared memory (max 227 KiB)", sc->smem);
+    // two resident CTAs per SM (registers capped at 64) for the generic
+    // complex64 kernels, when asked for, or by default where two tiles fit
+    const bool generic = !pl->form && pl->esize == 8 && B > 1 &&
+                         !stage_kernel_fn_special_f32(lgL, sc->lgW, sc->lgK, mode);
+    const bool two = generic && (pl->req_ctas == 2 ||
+                                 (pl->req_ctas == 0 && kDefaultTwoCtas && sc->smem <= 113 * 1024));
+    if (two) sc->fn = stage_kernel_fn_f32(lgL, 2);
     PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        227 * 1024));
     return PACO_OK;
@@ -191,6 +199,8 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
         o->dtype != PACO_C64_TC_FP16)
         return fail(PACO_ERR_UNSUPPORTED, "dtype %d is not built", (int)o->dtype);
     if (o->batch < 0) return fail(PACO_ERR_INVALID_ARG, "batch %lld < 0", (long long)o->batch);
+    if (o->ctas_per_sm < 0 || o->ctas_per_sm > 2)
+        return fail(PACO_ERR_INVALID_ARG, "ctas_per_sm=%d must be 0, 1 or 2", o->ctas_per_sm);
     const int t = ilog2_exact(o->b);
     const int l1 = ilog2_exact(o->N1), l2 = ilog2_exact(o->N2);
     if (l1 < 1 || l1 % t) return fail(PACO_ERR_INVALID_ARG, "N1=%lld is not a power of b=%d (>= b)", (long long)o->N1, o->b);
@@ -217,6 +227,7 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
     pl->b = o->b; pl->t = t; pl->p = p; pl->m1 = m1; pl->m2 = m2;
     pl->dtype = o->dtype;
     pl->esize = (o->dtype == PACO_C128) ? 16 : 8;
+    pl->req_ctas = o->ctas_per_sm;
     pl->form = (o->dtype == PACO_C64_TC_BF16X3) ? TC_BF16X3 : (o->dtype == PACO_C64_TC_FP16) ? TC_FP16 : TC_NONE;
     if (pl->form) {
         paco_status_t ts = tc_table_create(pl->form, &pl->tc);

@@ -42,6 +42,7 @@ struct paco_plan {
     size_t ctr_words = 0;
     int num_sms = 0;
     int form = 0;                  // tensor-core precision form (paco_tc.cuh), 0 = plain
+    int req_ctas = 0;              // requested CTAs per SM of the stage kernels (0 = default)
     void *tc = nullptr;            // its fragment table
     // uneven batch (paco_plan_create_batched): N = total elements, batch = 1
     paco::BatchedState *bs = nullptr;

@@ -11,31 +11,36 @@ template <typename R, int LGL>
 struct StageKernel {
     static constexpr int A = 1 << ((LGL + 1) / 2);
     static constexpr int B = 1 << (LGL / 2);
-    static const void *fn()
+    // minb: resident CTAs per SM the kernel is compiled for (2 caps the
+    // registers at 64 per thread; complex64 only)
+    static const void *fn(int minb)
     {
         if constexpr (B == 1) return reinterpret_cast<const void *>(&paco_stage_kernel_b1<R, A>);
-        else return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B>);
+        else if constexpr (sizeof(R) == 4) {
+            if (minb == 2) return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B, -1, -1, 0, 2>);
+            return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B>);
+        } else return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B>);
     }
 };
 
 template <typename R>
-const void *stage_kernel_fn(int lgL)
+const void *stage_kernel_fn(int lgL, int minb)
 {
     switch (lgL) {
-    case 1: return StageKernel<R, 1>::fn();
-    case 2: return StageKernel<R, 2>::fn();
-    case 3: return StageKernel<R, 3>::fn();
-    case 4: return StageKernel<R, 4>::fn();
-    case 5: return StageKernel<R, 5>::fn();
-    case 6: return StageKernel<R, 6>::fn();
-    case 7: return StageKernel<R, 7>::fn();
-    case 8: return StageKernel<R, 8>::fn();
-    case 9: return StageKernel<R, 9>::fn();
-    case 10: return StageKernel<R, 10>::fn();
-    case 11: return StageKernel<R, 11>::fn();
-    case 12: return StageKernel<R, 12>::fn();
-    case 13: return StageKernel<R, 13>::fn();
-    case 14: return StageKernel<R, 14>::fn();
+    case 1: return StageKernel<R, 1>::fn(minb);
+    case 2: return StageKernel<R, 2>::fn(minb);
+    case 3: return StageKernel<R, 3>::fn(minb);
+    case 4: return StageKernel<R, 4>::fn(minb);
+    case 5: return StageKernel<R, 5>::fn(minb);
+    case 6: return StageKernel<R, 6>::fn(minb);
+    case 7: return StageKernel<R, 7>::fn(minb);
+    case 8: return StageKernel<R, 8>::fn(minb);
+    case 9: return StageKernel<R, 9>::fn(minb);
+    case 10: return StageKernel<R, 10>::fn(minb);
+    case 11: return StageKernel<R, 11>::fn(minb);
+    case 12: return StageKernel<R, 12>::fn(minb);
+    case 13: return StageKernel<R, 13>::fn(minb);
+    case 14: return StageKernel<R, 14>::fn(minb);
     default: return nullptr;
     }
 }
