@@ -454,7 +454,7 @@ def run_other(args, ranks, local):
         us = mor(statistics.median(per)) * 1e3
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
-        e2e = e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 20), stream,
+        e2e = None if args.no_e2e else e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 20), stream,
                        1.0, "transforms/s", N * 8, N * 8, "paco_execute_host (pinned host buffers)", mor, world,
                        ranks.barrier)
         line = dict(base, value=us, unit="us (median latency per transform)", higher_is_better=False,
@@ -496,7 +496,7 @@ def run_other(args, ranks, local):
         dom_ms = max(s1, s2)
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
-        e2e = e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1), stream,
+        e2e = None if args.no_e2e else e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1), stream,
                        flop / 1e9, "GFLOP/s", N * 16, N * 16, "paco_execute_host (pinned host buffers)", mor,
                        world, ranks.barrier)
         hr = hbm_roofline("stage1" if s1 >= s2 else "stage2", 32.0 * N, dom_ms)
@@ -535,7 +535,7 @@ def run_other(args, ranks, local):
         ms = mor(tot) / K
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
-        e2e = e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1), stream,
+        e2e = None if args.no_e2e else e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1), stream,
                        flop / 1e9, "GFLOP/s", total * 8, total * 8, "paco_execute_host (pinned host buffers)", mor,
                        world, ranks.barrier)
         cfg = {str(int(n)): dict(zip(("b", "N1", "ctas_per_sm", "lag"), plan.config(int(n))))
@@ -595,7 +595,7 @@ def run_other(args, ranks, local):
         pl = paco.Plan(N1, N2, 4, B, hdt)
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
-        line["e2e"] = e2e_host(lambda: pl.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1),
+        line["e2e"] = None if args.no_e2e else e2e_host(lambda: pl.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1),
                                stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
                                "paco_execute_host (pinned host buffers)", mor, world, ranks.barrier)
     elif wl == "U":
@@ -666,7 +666,7 @@ def run_other(args, ranks, local):
             loss = (w * (yv.real ** 2 + yv.imag ** 2)).sum()
             loss.backward()
             gh.copy_(xd.grad, non_blocking=True)
-        e2e = e2e_host(step_host, max(args.e2e_steps, 1), stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
+        e2e = None if args.no_e2e else e2e_host(step_host, max(args.e2e_steps, 1), stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
                        "torch.autograd through PacoFFT (pinned host input and gradient)", mor, world, ranks.barrier)
         line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s (forward + backward transforms)",
                     higher_is_better=True, ms_per_step=ms, dtype="f32",
