@@ -128,6 +128,24 @@ __device__ __forceinline__ float2 f2mul(float2 a, float2 b)
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Twiddles of a thread computed in registers from a few table entries (a
+// shared-memory read costs more than the products here: the consumers are
+// bound by shared-memory traffic).  seq8: out[k] = b * s^k, k < 8, from b,
+// s and s^4; at most four roundings on top of the tables'.
+__device__ __forceinline__ void seq8(float2 *out, float2 b, float2 s1, float2 s4)
+{
+    const float2 s2 = f2mul(s1, s1), s3 = f2mul(s2, s1);
+    out[0] = b;
+    out[1] = f2mul(b, s1);
+    out[2] = f2mul(b, s2);
+    out[3] = f2mul(b, s3);
+    const float2 b4 = f2mul(b, s4);
+    out[4] = b4;
+    out[5] = f2mul(b4, s1);
+    out[6] = f2mul(b4, s2);
+    out[7] = f2mul(b4, s3);
+}
+
 // exchange slot of sequence (jl, c) in the stage-1 A tile: conflict-free both
 // when lanes run over c (pass 1) and over jl then c (pass 2)
 __device__ __forceinline__ int slot_s1a(int jl, int c) { return c * 4 + (jl ^ ((c >> 2) & 3)); }
@@ -487,9 +505,18 @@ __device__ __forceinline__ void pass1_regs(const PanelArgs &a, const Tile &d, cx
         for (int r = 0; r < 16; ++r) v[r].y = -v[r].y;
     }
     dft16(v);
+    // w_128^{-s t8} = z^s, z = w_128^{-t8}: z^(4a + c) = z4^a * z^c from the
+    // table entries z, z^4, z^8 (s = 1, 4, 8 of w16[s * 8 + t8])
+    const float2 z1 = w16[8 + t8], z4 = w16[32 + t8], z8 = w16[64 + t8];
+    const float2 z2 = f2mul(z1, z1), z3 = f2mul(z2, z1), z12 = f2mul(z8, z4);
+    const float2 zl[4] = {make_float2(1.f, 0.f), z1, z2, z3};
+    const float2 zh[4] = {make_float2(1.f, 0.f), z4, z8, z12};
 #pragma unroll
     for (int s = 1; s < 16; ++s) {
-        const float2 w = w16[s * 8 + t8];
+        float2 w;
+        if ((s & 3) == 0) w = zh[s >> 2];
+        else if ((s >> 2) == 0) w = zl[s & 3];
+        else w = f2mul(zh[s >> 2], zl[s & 3]);
         const float2 p = f2mul(make_float2(v[s].x, v[s].y), w);
         v[s].x = p.x; v[s].y = p.y;
     }
@@ -515,13 +542,18 @@ __device__ __forceinline__ void pass2_store(const PanelArgs &a, const Tile &d, c
         const int jlo = j0 + jl;
         float2 *dst = buf + ((size_t)(c0 + cc) * 16 + (jlo >> 3)) * (A * 8) + (jlo & 7);
         const unsigned long long pol = policy_evict_last();
+        // TW[klo][jl] = w_L^{-klo jlo}, klo = 2 gp + h + 16 k: b_h * s^k
+        const float2 s1 = TW[16 * 4 + jl], s4 = TW[64 * 4 + jl];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < 2; ++h) {
+            float2 tw[8];
+            seq8(tw, TW[(2 * gp + h) * 4 + jl], s1, s4);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int klo = 2 * gp + h + 16 * k;
-                st_hint(dst + klo * 8, f2mul(make_float2(v[8 * h + k].x, v[8 * h + k].y), TW[klo * 4 + jl]), pol);
+                st_hint(dst + klo * 8, f2mul(make_float2(v[8 * h + k].x, v[8 * h + k].y), tw[k]), pol);
             }
+        }
     } else if (a.mode == 1) {
         const int cl = d.t >> 1, k0 = (d.t & 1) * 64;
         const unsigned cglob = (unsigned)(colbase + cl);
@@ -531,15 +563,20 @@ __device__ __forceinline__ void pass2_store(const PanelArgs &a, const Tile &d, c
         float2 *dst = gout + boff + (long long)urow * a.out_ld + k0 + k;
         const float2 e1 = E1[k];
         const unsigned long long pol = policy_evict_first();
+        // E2[khi] = w_N^{-128 khi c}, khi = 2 gp + h + 16 kk: (e1 E2[2 gp + h]) * s^kk
+        const float2 s1 = E2[16], s4 = E2[64];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < 2; ++h) {
+            float2 tw[8];
+            seq8(tw, f2mul(e1, E2[2 * gp + h]), s1, s4);
 #pragma unroll
             for (int kk = 0; kk < 8; ++kk) {
                 const int khi = 2 * gp + h + 16 * kk;
-                float2 y = f2mul(f2mul(make_float2(v[8 * h + kk].x, v[8 * h + kk].y), e1), E2[khi]);
+                float2 y = f2mul(make_float2(v[8 * h + kk].x, v[8 * h + kk].y), tw[kk]);
                 if (a.conj) y.y = -y.y;
                 st_hint(dst + A * khi, y, pol);
             }
+        }
     } else if (!d.isB) {
         // scratch layout [k_lo][j_lo][v]
         const int jlo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
@@ -547,13 +584,18 @@ __device__ __forceinline__ void pass2_store(const PanelArgs &a, const Tile &d, c
         pass2(v, sm, gp, vv);
         float2 *dst = buf + (size_t)jlo * a.P + v0 + vv;
         const unsigned long long pol = policy_evict_last();
+        // TW[klo] = w_L^{-klo jlo}, klo = 2 gp + h + 16 k: b_h * s^k
+        const float2 s1 = TW[16 * 4], s4 = TW[64 * 4];
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < 2; ++h) {
+            float2 tw[8];
+            seq8(tw, TW[(2 * gp + h) * 4], s1, s4);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const int klo = 2 * gp + h + 16 * k;
-                st_hint(dst + (size_t)klo * B * a.P, f2mul(make_float2(v[8 * h + k].x, v[8 * h + k].y), TW[klo * 4]), pol);
+                st_hint(dst + (size_t)klo * B * a.P, f2mul(make_float2(v[8 * h + k].x, v[8 * h + k].y), tw[k]), pol);
             }
+        }
     } else {
         const int klo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
         const int vv = tid & 63, gp = tid >> 6;
