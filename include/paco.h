@@ -253,6 +253,20 @@ paco_status_t paco_plan_create_batched_ex(paco_plan_t **out, const int64_t *leng
 paco_status_t paco_plan_batched_config(const paco_plan_t *plan, int64_t length, int *b, int *N1,
                                        int *ctas_per_sm, int *lag);
 
+/*
+ * paco_debug_set_waits -- test hook for the kernels' bounded waits (the
+ * paper has no counterpart).  The pipelined kernels (the 2^14 panel stages,
+ * the uneven-batch kernel) wait on completion counters of other CTAs; each
+ * wait gives up after a poll limit and records PACO_ERR_TIMEOUT in the plan's
+ * status word (read by paco_plan_check) instead of hanging.  spin_limit
+ * replaces the default poll limit (0 restores it); wait_bias is added to every
+ * counter target, so with wait_bias > 0 no such wait can be met: the next
+ * execution of the plan returns garbage and paco_plan_check reports
+ * PACO_ERR_TIMEOUT, and the CUDA context stays usable.  Set both to 0 for
+ * normal use.  Returns PACO_ERR_INVALID_ARG for a NULL plan.
+ */
+paco_status_t paco_debug_set_waits(paco_plan_t *plan, unsigned spin_limit, unsigned wait_bias);
+
 /* Largest batch that paco_execute_noalloc accepts. */
 #define PACO_NOALLOC_MAX_BATCH 16
 

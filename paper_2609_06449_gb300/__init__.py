@@ -120,6 +120,8 @@ def _load():
     pi = ctypes.POINTER(i32)
     L.paco_plan_batched_config.argtypes = [vp, i64, pi, pi, pi, pi]
     L.paco_plan_batched_config.restype = i32
+    L.paco_debug_set_waits.argtypes = [vp, ctypes.c_uint, ctypes.c_uint]
+    L.paco_debug_set_waits.restype = i32
     L.paco_execute_noalloc.argtypes = [vp, vp, i32, i64, i32, vp]
     L.paco_execute_noalloc.restype = i32
     return L
@@ -225,6 +227,10 @@ class Plan:
 
     def check(self) -> None:
         _check(lib.paco_plan_check(self._h))
+
+    def debug_set_waits(self, spin_limit: int = 0, wait_bias: int = 0) -> None:
+        """Test hook of the bounded waits (``paco_debug_set_waits``)."""
+        _check(lib.paco_debug_set_waits(self._h, int(spin_limit), int(wait_bias)))
 
 
 class BatchedPlan(Plan):

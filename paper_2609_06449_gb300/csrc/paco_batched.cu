@@ -80,6 +80,7 @@ struct BatchedArgs {
     unsigned *ctr;                 // [0] queue head, [1 + i] Phase I tiles done of transform i
     int *status;
     unsigned spin_limit;
+    unsigned wait_bias;            // added to the Phase III wait target (0; tests of the bounded waits)
     int conj;
 };
 
@@ -377,7 +378,7 @@ __global__ void __launch_bounds__(batched::NT, MINB) paco_batched_kernel(const _
         const long long boff = item.off;
         if (item.kind == 2) {
             if (tid == 0) {
-                const unsigned need = (unsigned)ld.ntiles1;
+                const unsigned need = (unsigned)ld.ntiles1 + a.wait_bias;
                 const unsigned *c = a.ctr + 1 + item.a;
                 unsigned n = 0;
                 int ok = 1;
@@ -654,7 +655,8 @@ static paco_status_t launch(const paco_plan *pl, const BatchedState *bs, const v
     a.out = out;
     a.ctr = bs->d_ctr;
     a.status = pl->d_status;
-    a.spin_limit = 1u << 24;
+    a.spin_limit = pl->dbg_spin_limit ? pl->dbg_spin_limit : 1u << 24;
+    a.wait_bias = pl->dbg_wait_bias;
     a.conj = (dir == 1);
     PACO_CUDA_TRY(cudaMemsetAsync(bs->d_ctr, 0, bs->ctr_words * sizeof(unsigned), stream));
     const int grid = std::min<long long>(bs->grid, std::max(1, bs->nitems));

@@ -452,7 +452,8 @@ static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int m
     a.twN_lo = pl->twN_lo;
     a.twN_hi = pl->twN_hi;
     a.twN_lo_bits = pl->twN_lo_bits;
-    a.spin_limit = 1u << 22;
+    a.spin_limit = pl->dbg_spin_limit ? pl->dbg_spin_limit : 1u << 22;
+    a.dep_bias = pl->dbg_wait_bias;
     if (mode == 1) {
         a.C = (int)pl->N2;
         a.out_ld = (int)pl->N1;
@@ -639,6 +640,14 @@ extern "C" paco_status_t paco_plan_check(paco_plan_t *pl)
     PACO_CUDA_TRY(cudaMemset(pl->d_status, 0, sizeof(int)));
     if (h == PACO_ERR_TIMEOUT) return fail(PACO_ERR_TIMEOUT, "a bounded device wait gave up");
     if (h != 0) return fail(PACO_ERR_DEVICE, "device status word %d", h);
+    return PACO_OK;
+}
+
+extern "C" paco_status_t paco_debug_set_waits(paco_plan_t *pl, unsigned spin_limit, unsigned wait_bias)
+{
+    if (!pl) return fail(PACO_ERR_INVALID_ARG, "plan is NULL");
+    pl->dbg_spin_limit = spin_limit;
+    pl->dbg_wait_bias = wait_bias;
     return PACO_OK;
 }
 

@@ -74,6 +74,7 @@ struct PanelArgs {
     int conj;
     unsigned spin_limit;
     int use_tensor;                // 1: tiles arrive by tensor TMA, 0: by bulk copies
+    unsigned dep_bias;             // added to every dependency target (0; tests of the bounded waits)
 };
 
 namespace panel {
@@ -297,7 +298,7 @@ __device__ __forceinline__ int acquire_dep(const PanelArgs &a, const unsigned *d
     int ok = 1;
     if ((threadIdx.x & 31) == 0) {
         unsigned it = 0;
-        while (panel::ld_acquire(dep) < (unsigned)tiles_per_phase(a)) {
+        while (panel::ld_acquire(dep) < (unsigned)tiles_per_phase(a) + a.dep_bias) {
             if (++it > a.spin_limit) {
                 atomicExch(a.status, 5 /* PACO_ERR_TIMEOUT */);
                 ok = -1;

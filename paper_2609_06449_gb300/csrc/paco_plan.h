@@ -43,6 +43,8 @@ struct paco_plan {
     int num_sms = 0;
     int form = 0;                  // tensor-core precision form (paco_tc.cuh), 0 = plain
     int req_ctas = 0;              // requested CTAs per SM of the stage kernels (0 = default)
+    unsigned dbg_spin_limit = 0;   // paco_debug_set_waits: poll limit of the bounded waits (0 = default)
+    unsigned dbg_wait_bias = 0;    // paco_debug_set_waits: added to the dependency targets
     void *tc = nullptr;            // its fragment table
     // uneven batch (paco_plan_create_batched): N = total elements, batch = 1
     paco::BatchedState *bs = nullptr;
