@@ -74,3 +74,35 @@ def test_tc_form_full_size_sampled(form):
     got = y.cpu().numpy()[ks]
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err <= bound(form, N), err
+
+
+@pytest.mark.parametrize("form", ["plain", "bf16x3", "fp16"])
+def test_precision_workload_full_size(form):
+    """The precision benchmark's configuration: 16 transforms of 2^24
+    (4096 x 4096, b = 4) with log-uniform magnitudes 1e-4..1e4 and uniform
+    phases.  Four sampled outputs of every transform against the oracle's
+    single-coefficient DFT, and Parseval per transform."""
+    from paco_inputs import loguniform
+    N1 = N2 = 4096
+    N, B = N1 * N2, 16
+    dt = {"plain": paco.C64, "bf16x3": paco.C64_TC_BF16X3, "fp16": paco.C64_TC_FP16}[form]
+    x = np.concatenate([loguniform(N, 100 + i, np.complex64) for i in range(B)])
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xt)
+    plan = paco.Plan(N1, N2, 4, B, dt)
+    plan.execute(xt, y, -1)
+    torch.cuda.synchronize()
+    plan.check()
+    bound_ = 5e-7 * 24 if form != "fp16" else 1e-3
+    ex = (xt.view(B, N).abs().double() ** 2).sum(1)
+    ey = (y.view(B, N).abs().double() ** 2).sum(1)
+    assert float(((ey / (N * ex)) - 1).abs().max()) <= (1e-5 if form != "fp16" else 2e-3)
+    yh = y.cpu().numpy().reshape(B, N)
+    rng = np.random.default_rng(9)
+    for i in range(B):
+        ks = rng.integers(0, N, 4)
+        ref = oracle.dft_at(x[i * N:(i + 1) * N].astype(np.complex128), ks)
+        # relative to the transform's rms output (single coefficients can be small)
+        rms = math.sqrt(float(ey[i]) / N)
+        err = np.max(np.abs(yh[i, ks] - ref)) / rms
+        assert err <= bound_ * 4, (i, err)
