@@ -452,6 +452,8 @@ def run_other(args, ranks, local):
         tot, per, clocks = timed(lambda: plan.execute(x, y, -1, stream))
         plan.check()
         us = mor(statistics.median(per)) * 1e3
+        acc = {"rel_l2": rel_l2_vs_oracle(y.cpu().numpy(), xh.numpy()),
+               "measured_on": "the timed transform, vs the FP64 oracle"}
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
         e2e = None if args.no_e2e else e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 20), stream,
@@ -465,7 +467,7 @@ def run_other(args, ranks, local):
                             "l2": "input fits in L2: latency-bound by design, no flush"},
                     roofline=dict(hbm_roofline("stage kernels (2 launches)", 32.0 * N, statistics.median(per)),
                                   bound="latency"),
-                    gflops=5.0 * N * 16 / (us * 1e-6) / 1e9,
+                    gflops=5.0 * N * 16 / (us * 1e-6) / 1e9, accuracy=acc,
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=16), gpu_launches=2 * K, clocks=clocks)
     elif wl == "B128":
         N1, N2 = 1 << 13, 1 << 14
@@ -500,12 +502,22 @@ def run_other(args, ranks, local):
                        flop / 1e9, "GFLOP/s", N * 16, N * 16, "paco_execute_host (pinned host buffers)", mor,
                        world, ranks.barrier)
         hr = hbm_roofline("stage1" if s1 >= s2 else "stage2", 32.0 * N, dom_ms)
+        import oracle
+        plan.execute(x, y, -1, stream)
+        torch.cuda.synchronize()
+        ks = np.random.default_rng(5).integers(0, N, 8)
+        ref = oracle.dft_at(xh.numpy(), ks, threads=0)
+        got = y[torch.from_numpy(ks).cuda()].cpu().numpy()
+        rms = math.sqrt(float((x.abs() ** 2).sum().item()))     # Parseval: rms of y = sqrt(sum |x|^2)
+        acc = {"max_abs_err_over_rms": float(np.max(np.abs(got - ref)) / rms),
+               "measured_on": "8 sampled coefficients vs the oracle's single-coefficient DFT"}
         line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s", higher_is_better=True,
                     ms_per_step=ms, dtype="f64",
                     config={"workload": "c128 1-D DFT N=2^27 as N1=2^13 x N2=2^14, b=2, p=128, forward",
                             "N1": N1, "N2": N2, "b": 2, "p": 128, "batch": 1,
                             "input": "Re, Im i.i.d. U[-1,1), seed = rank", "l2": "inputs larger than L2"},
                     stage_ms={"stage1": s1, "stage2": s2}, hbm_gbs_effective=64.0 * N * world / (ms * 1e-3) / 1e9,
+                    accuracy=acc,
                     roofline={"bound": "alu", "kernel": hr["kernel"],
                               "achieved": flop / 2 / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak / 1e3,
                               "unit": "TFLOP/s (nominal 5N log2 N flops, half per stage)",
@@ -540,6 +552,18 @@ def run_other(args, ranks, local):
                        world, ranks.barrier)
         cfg = {str(int(n)): dict(zip(("b", "N1", "ctas_per_sm", "lag"), plan.config(int(n))))
                for n in np.unique(lengths)}
+        plan.execute(x, y, -1, stream)
+        torch.cuda.synchronize()
+        offs = np.concatenate([[0], np.cumsum(lengths)])
+        rng = np.random.default_rng(3)
+        worst = 0.0
+        for n in np.unique(lengths):
+            for i in rng.choice(np.flatnonzero(lengths == n), size=2, replace=False):
+                a_, b_ = int(offs[i]), int(offs[i + 1])
+                e_ = rel_l2_vs_oracle(y[a_:b_].cpu().numpy(), xh[a_:b_].numpy())
+                worst = max(worst, e_ / (5e-7 * math.log2(n)))
+        acc = {"max_rel_l2_over_bound": worst,
+               "measured_on": "2 sampled transforms of every length vs the oracle; bound 5e-7*log2(N_i)"}
         line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s", higher_is_better=True,
                     ms_per_step=ms, dtype="f32",
                     config={"workload": "uneven batch: 4096 c64 transforms, log2 lengths uniform over 8..20 "
@@ -547,7 +571,7 @@ def run_other(args, ranks, local):
                                         "launch", "transforms": int(len(lengths)), "total_elements": total,
                             "input": "Re, Im i.i.d. N(0,1), seed = rank", "l2": "inputs larger than L2",
                             "autotuned": cfg, "plan_seconds": t_plan},
-                    hbm_gbs_effective=32.0 * total * world / (ms * 1e-3) / 1e9,
+                    hbm_gbs_effective=32.0 * total * world / (ms * 1e-3) / 1e9, accuracy=acc,
                     roofline=hbm_roofline("paco_batched_kernel (1 launch)", 16.0 * total, statistics.mean(per)),
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=18), gpu_launches=K, clocks=clocks)
     elif wl == "D":
@@ -661,6 +685,16 @@ def run_other(args, ranks, local):
             step()
         tot, per, clocks = timed(step)
         flop = 2 * 5.0 * N * 20 * B
+        import oracle
+        step()
+        torch.cuda.synchronize()
+        x0 = xh[0].numpy().astype(np.complex128)
+        w0 = wh[0].numpy().astype(np.float64)
+        # d/dx of sum(w |F x|^2) in PyTorch's convention: 2 F^H (w * F x)
+        gref = 2.0 * oracle.fft((w0 * oracle.fft(x0.reshape(1, -1))).reshape(1, -1), dir=+1).reshape(-1)
+        g0 = x.grad[0].detach().cpu().numpy().astype(np.complex128)
+        acc = {"grad_rel_l2": float(np.linalg.norm(g0 - gref) / np.linalg.norm(gref)),
+               "measured_on": "gradient of transform 0 vs the analytic adjoint 2 F^H (w F x) from the oracle"}
         ms = mor(tot) / K
         gh = torch.empty_like(xh).pin_memory()
 
@@ -676,6 +710,7 @@ def run_other(args, ranks, local):
                     config={"workload": "256 x c64 1-D DFT N=2^20 (1024 x 1024, b=4): loss = sum(w |FFT(x)|^2), "
                                         "forward + backward (conjugate transform) through torch.autograd",
                             "input": "x Re, Im i.i.d. N(0,1); w U[0,1)", "l2": "inputs larger than L2"},
+                    accuracy=acc,
                     roofline=hbm_roofline("stage kernels (4 launches + torch loss ops)", 4 * 16.0 * N * B, ms),
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=20), gpu_launches=4 * K, clocks=clocks)
     if rank == 0:
