@@ -226,7 +226,7 @@ const char *paco_version(void);
  * sum_{j<i} lengths[j]); each is computed as by a single-length plan (natural
  * order in and out).  The default constructor autotunes: it times candidate
  * configurations on plan-owned scratch buffers (allocated and freed inside
- * the call, up to 2 x 256 MiB) and keeps the fastest.  Returns
+ * the call, up to 2 x 512 MiB) and keeps the fastest.  Returns
  * PACO_ERR_UNSUPPORTED for other dtypes or lengths, PACO_ERR_INVALID_ARG for
  * a NULL list with count > 0.  Execution of such a plan is one
  * cudaMemsetAsync of its counters and one kernel launch on `stream`, so it can
