@@ -217,6 +217,31 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                 x.y *= csign;
                 v[u * RA1 + r] = x;
             }
+            if constexpr (FORM != TC_NONE && RA1 == 16 && RA2 > 1) {
+                // tensor-core contraction, twiddled and stored straight from the
+                // accumulator fragments: lane n's sequence is bfi of lane n
+                float acc[4][2][4];
+                float sb;
+                tc_contract<FORM>(v + u * RA1, tc_tab, tc_ws, acc, sb);
+                const int lane = tid & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int n = 8 * nt + 2 * q + h;
+                        const float sbn = (FORM == TC_FP16) ? __shfl_sync(0xffffffffu, sb, n) : 1.f;
+                        const int bfn = (tid - lane) + n + NT * u;
+                        const int seqn = bfn & (S1 - 1), jjn = bfn / S1;
+#pragma unroll
+                        for (int si = 0; si < 2; ++si) {
+                            const int s = g + 8 * si;
+                            C y = tc_frag_out(acc, nt, h, si, sbn);
+                            if (s > 0) y = cmul(y, twA[s * jjn]);
+                            sm[(jjn + RA2 * s) * P1 + seqn] = y;
+                        }
+                    }
+                continue;
+            }
             if constexpr (FORM != TC_NONE && RA1 == 16) tc_dft16<FORM>(v + u * RA1, tc_tab, tc_ws);
             else dft<RA1>(v + u * RA1);
             if constexpr (RA2 > 1) {
@@ -317,6 +342,33 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
         }
 #pragma unroll
         for (int r = 0; r < RB1; ++r) v[u * RB1 + r] = sm[al * P2 + ((jj + RB2 * r) << lgW) + col];
+        if constexpr (FORM != TC_NONE && RB1 == 16 && RB2 > 1) {
+            // as in F1: straight from the accumulator fragments (this pass uses
+            // the col-fastest thread mapping whenever RB2 > 1)
+            float acc[4][2][4];
+            float sb;
+            tc_contract<FORM>(v + u * RB1, tc_tab, tc_ws, acc, sb);
+            const int lane = tid & 31, g = lane >> 2, q = lane & 3;
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int n = 8 * nt + 2 * q + h;
+                    const float sbn = (FORM == TC_FP16) ? __shfl_sync(0xffffffffu, sb, n) : 1.f;
+                    const int bfn = (tid - lane) + n + NT * u;
+                    const int coln = bfn & (W - 1);
+                    const int jjn = (bfn >> lgW) % RB2;
+                    const int aln = (bfn >> lgW) / RB2;
+#pragma unroll
+                    for (int si = 0; si < 2; ++si) {
+                        const int s = g + 8 * si;
+                        C y = tc_frag_out(acc, nt, h, si, sbn);
+                        if (s > 0) y = cmul(y, twB[s * jjn]);
+                        sm[aln * P2 + ((jjn + RB2 * s) << lgW) + coln] = y;
+                    }
+                }
+            continue;
+        }
         if constexpr (FORM != TC_NONE && RB1 == 16) tc_dft16<FORM>(v + u * RB1, tc_tab, tc_ws);
         else dft<RB1>(v + u * RB1);
         if constexpr (RB2 > 1) {

@@ -88,18 +88,23 @@ __device__ __forceinline__ uint32_t pack_f16(float lo, float hi)
     return *reinterpret_cast<uint32_t *>(&p);
 }
 
-// Warp-collective: v[0..16) of every lane -> its natural-order 16-point DFT.
-// All 32 lanes must call it together.  tab: the fragment table in shared
-// memory; ws: this warp's staging area (WARP_WORDS words).
+// Warp-collective contraction: v[0..16) of every lane (its 16-point
+// sequence) -> the accumulator fragments of [Re y; Im y] for the warp's 32
+// sequences: acc[nt][mt][i] is row m = 16 mt + g + 8 (i >> 1) (m < 16: Re of
+// frequency m, else Im of m - 16) and column n = 8 nt + 2 q + (i & 1) (lane n's
+// sequence), g = lane / 4, q = lane % 4.  scale_back: this lane's sequence
+// scale (FP16 form; 1 otherwise).  All 32 lanes must call it together; ws is
+// free again when it returns.
 template <int FORM>
-__device__ __forceinline__ void tc_dft16(cx<float> *v, const uint4 *tab, uint32_t *ws)
+__device__ __forceinline__ void tc_contract(const cx<float> *v, const uint4 *tab, uint32_t *ws,
+                                            float (&acc)[4][2][4], float &scale_back)
 {
     using T = TcForm<FORM>;
     const int lane = threadIdx.x & 31;
     const int g = lane >> 2, q = lane & 3;
     // ---- operand terms of this lane's sequence, row `lane` of each plane;
     //      words 0..3 and 4..7 swap on rows with bit 2 set (conflict-free reads)
-    float scale_back = 1.f;
+    scale_back = 1.f;
     {
         const int sw = ((lane >> 2) & 1) << 2;
         if constexpr (FORM == TC_BF16X3) {
@@ -150,47 +155,59 @@ __device__ __forceinline__ void tc_dft16(cx<float> *v, const uint4 *tab, uint32_
         }
     }
     __syncwarp();
-    // ---- contraction: tile (mt, nt) of [Re y; Im y]
-    float acc[4][2][4];
+    // ---- contraction: tile (mt, nt) of [Re y; Im y].  The matrix fragments
+    //      of one (mt, K half) are loaded once and used for all four groups of
+    //      eight sequences (the operand fragments, 4-byte reads, are re-read).
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) acc[nt][mt][0] = acc[nt][mt][1] = acc[nt][mt][2] = acc[nt][mt][3] = 0.f;
     const int rsw = ((g >> 2) & 1) << 2;        // swap of the source row n = 8 nt + g
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt) {
-        uint32_t b[T::TB][2][2];
+    for (int mt = 0; mt < 2; ++mt) {
 #pragma unroll
-        for (int tb = 0; tb < T::TB; ++tb)
+        for (int ks = 0; ks < 2; ++ks) {
+            uint4 af[T::TA];
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint32_t *row = ws + ((tb * 2 + ks) * 32 + 8 * nt + g) * 8;
-                b[tb][ks][0] = row[q ^ rsw];           // k = 2q, 2q+1
-                b[tb][ks][1] = row[(q + 4) ^ rsw];     // k = 2q+8, 2q+9
-            }
+            for (int ta = 0; ta < T::TA; ++ta) af[ta] = tab[((ta * 2 + mt) * 2 + ks) * 32 + lane];
 #pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            float *d = acc[nt][mt];
-            d[0] = d[1] = d[2] = d[3] = 0.f;
+            for (int nt = 0; nt < 4; ++nt) {
+                uint32_t bq[T::TB][2];
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
+                for (int tb = 0; tb < T::TB; ++tb) {
+                    const uint32_t *row = ws + ((tb * 2 + ks) * 32 + 8 * nt + g) * 8;
+                    bq[tb][0] = row[q ^ rsw];           // k = 2q, 2q+1
+                    bq[tb][1] = row[(q + 4) ^ rsw];     // k = 2q+8, 2q+9
+                }
+                float *d = acc[nt][mt];
                 if constexpr (FORM == TC_BF16X3) {
-                    const uint4 a2 = tab[((2 * 2 + mt) * 2 + ks) * 32 + lane];
-                    const uint4 a1 = tab[((1 * 2 + mt) * 2 + ks) * 32 + lane];
-                    const uint4 a0 = tab[((0 * 2 + mt) * 2 + ks) * 32 + lane];
                     // smallest products first
-                    mma_bf16(d, a2, b[0][ks][0], b[0][ks][1]);
-                    mma_bf16(d, a1, b[1][ks][0], b[1][ks][1]);
-                    mma_bf16(d, a0, b[2][ks][0], b[2][ks][1]);
-                    mma_bf16(d, a1, b[0][ks][0], b[0][ks][1]);
-                    mma_bf16(d, a0, b[1][ks][0], b[1][ks][1]);
-                    mma_bf16(d, a0, b[0][ks][0], b[0][ks][1]);
+                    mma_bf16(d, af[2], bq[0][0], bq[0][1]);
+                    mma_bf16(d, af[1], bq[1][0], bq[1][1]);
+                    mma_bf16(d, af[0], bq[2][0], bq[2][1]);
+                    mma_bf16(d, af[1], bq[0][0], bq[0][1]);
+                    mma_bf16(d, af[0], bq[1][0], bq[1][1]);
+                    mma_bf16(d, af[0], bq[0][0], bq[0][1]);
                 } else {
-                    const uint4 a1 = tab[((1 * 2 + mt) * 2 + ks) * 32 + lane];
-                    const uint4 a0 = tab[((0 * 2 + mt) * 2 + ks) * 32 + lane];
-                    mma_f16(d, a1, b[0][ks][0], b[0][ks][1]);
-                    mma_f16(d, a0, b[0][ks][0], b[0][ks][1]);
+                    mma_f16(d, af[1], bq[0][0], bq[0][1]);
+                    mma_f16(d, af[0], bq[0][0], bq[0][1]);
                 }
             }
         }
     }
-    __syncwarp();                               // every operand read before the result overwrites
+    __syncwarp();                               // every operand read: ws is free
+}
+
+// Warp-collective: v[0..16) of every lane -> its natural-order 16-point DFT
+// (the contraction, then the result transposed back through ws).
+template <int FORM>
+__device__ __forceinline__ void tc_dft16(cx<float> *v, const uint4 *tab, uint32_t *ws)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, q = lane & 3;
+    float acc[4][2][4];
+    float scale_back;
+    tc_contract<FORM>(v, tab, ws, acc, scale_back);
     // ---- result [n][m] (row stride 33), then each lane takes its row
     float *o = reinterpret_cast<float *>(ws);
 #pragma unroll
@@ -210,6 +227,13 @@ __device__ __forceinline__ void tc_dft16(cx<float> *v, const uint4 *tab, uint32_
         v[k].y = o[lane * 33 + 16 + k] * scale_back;
     }
     __syncwarp();                               // staging free for the next call
+}
+
+// Output (frequency s = g + 8 si, sequence n = 8 nt + 2 q + h) of the
+// fragments of tc_contract, unscaled by that sequence's factor.
+__device__ __forceinline__ cx<float> tc_frag_out(const float (&acc)[4][2][4], int nt, int h, int si, float sb)
+{
+    return make_cx<float>(acc[nt][0][h + 2 * si] * sb, acc[nt][1][h + 2 * si] * sb);
 }
 
 } // namespace paco
