@@ -405,6 +405,21 @@ def e2e_host(step_host, KE, stream, units, unit, h2d, d2h, api, max_over_ranks, 
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "api": api}
 
 
+def cufft_context(x, N: int, batch: int, flop: float, reps: int = 20):
+    """cuFFT (through torch.fft.fft) on the same input: context only, not
+    part of the measured path."""
+    import torch
+    try:
+        xv = x.view(batch, N)
+        stream = torch.cuda.current_stream()
+        tot, per = time_steps(lambda: torch.fft.fft(xv), reps, 3, stream)
+        ms = statistics.median(per)
+        return {"cufft_ms_per_step": ms, "cufft_gflops": flop / (ms * 1e-3) / 1e9,
+                "source": "torch.fft.fft (cuFFT C2C), same input, median of %d" % reps}
+    except Exception as e:  # report, do not hide
+        return {"cufft": f"failed: {e}"}
+
+
 def emit(line):
     print(json.dumps(line), flush=True)
 
@@ -517,7 +532,7 @@ def run_other(args, ranks, local):
                             "N1": N1, "N2": N2, "b": 2, "p": 128, "batch": 1,
                             "input": "Re, Im i.i.d. U[-1,1), seed = rank", "l2": "inputs larger than L2"},
                     stage_ms={"stage1": s1, "stage2": s2}, hbm_gbs_effective=64.0 * N * world / (ms * 1e-3) / 1e9,
-                    accuracy=acc,
+                    accuracy=acc, context=cufft_context(x, N, 1, flop),
                     roofline={"bound": "alu", "kernel": hr["kernel"],
                               "achieved": flop / 2 / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak / 1e3,
                               "unit": "TFLOP/s (nominal 5N log2 N flops, half per stage)",
@@ -611,7 +626,7 @@ def run_other(args, ranks, local):
                             "form_of_value": head,
                             "input": "log-uniform magnitudes 1e-4..1e4, uniform phases, seed = 100*rank + i",
                             "l2": "inputs larger than L2"},
-                    forms=forms,
+                    forms=forms, context=cufft_context(x, N, B, flop),
                     roofline=hbm_roofline(f"stage kernel ({head})", 16.0 * N * B,
                                           forms[head]["dominant_launch_ms"]),
                     e2e=None, cpu_baseline=cpu_leg(args, rank, world), gpu_launches=2 * K * len(forms), clocks=clocks)
@@ -710,7 +725,7 @@ def run_other(args, ranks, local):
                     config={"workload": "256 x c64 1-D DFT N=2^20 (1024 x 1024, b=4): loss = sum(w |FFT(x)|^2), "
                                         "forward + backward (conjugate transform) through torch.autograd",
                             "input": "x Re, Im i.i.d. N(0,1); w U[0,1)", "l2": "inputs larger than L2"},
-                    accuracy=acc,
+                    accuracy=acc, context=cufft_context(x.detach(), N, B, flop / 2),
                     roofline=hbm_roofline("stage kernels (4 launches + torch loss ops)", 4 * 16.0 * N * B, ms),
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=20), gpu_launches=4 * K, clocks=clocks)
     if rank == 0:
@@ -829,6 +844,7 @@ def main():
         tc["plain"].update({"ms_per_step": ms_step, "value": value, "unit": "GFLOP/s"})
 
     cpu = cpu_leg(args, rank, world, args.dtype)
+    context = cufft_context(x, N, 1, flop)
 
     if rank == 0:
         line = {
@@ -844,7 +860,7 @@ def main():
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": 2 * K, "clocks": clocks,
-            "tc_split": tc,
+            "tc_split": tc, "context": context,
         }
         print(json.dumps(line), flush=True)
     ranks.close()
