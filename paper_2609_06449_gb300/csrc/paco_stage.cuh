@@ -277,7 +277,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     for (int u = 0; u < NBF; ++u) {
         const int bfi = tid + NT * u;
         const int seq = bfi & (S1 - 1), hi = bfi / S1;   // hi = g (2 passes) or 0
-        const int jl = seq >> lgW, col = seq & (W - 1);
+        const int jl = seq >> lgW;
         const int jlo = rank * Bk + jl;
 #pragma unroll
         for (int k = 0; k < RF; ++k) {
