@@ -273,6 +273,20 @@ paco_status_t paco_plan_batched_config(const paco_plan_t *plan, int64_t length, 
  */
 paco_status_t paco_debug_set_waits(paco_plan_t *plan, unsigned spin_limit, unsigned wait_bias);
 
+/*
+ * paco_debug_batched_schedule -- test hook (host only, no GPU): the work
+ * queue an uneven-batch plan executes, in claim order, for `count` lengths
+ * (powers of two 2^4..2^20) and a Phase III lag of `lag_items` items.  Item k
+ * is kind[k] = 0 (a group of small transforms: group[index[k] ..
+ * index[k] + tile[k]) lists them), 1 (Phase I tile tile[k] of transform
+ * index[k]) or 2 (Phase III tile tile[k] of transform index[k]).  Returns the
+ * number of items, or -1 for bad arguments or when `cap` / `group_cap` is too
+ * small.
+ */
+int64_t paco_debug_batched_schedule(const int64_t *lengths, int64_t count, int64_t lag_items,
+                                    int32_t *kind, int32_t *index, int32_t *tile, int64_t cap,
+                                    int32_t *group, int64_t group_cap);
+
 /* Largest batch that paco_execute_noalloc accepts. */
 #define PACO_NOALLOC_MAX_BATCH 16
 

@@ -506,6 +506,69 @@ static LenCfg default_cfg(int lgN)
     return c;
 }
 
+// The work queue, in claim order (host only, no device state): transforms in
+// decreasing length (stable); small ones (N <= 2^13) in groups of up to
+// ITEM / N transforms of one length; every large transform's Phase I tiles
+// (N / ITEM of them), then its Phase III tiles once `lag` more items have
+// been queued after its last Phase I tile; small groups fill in at the end.
+// Every Phase III tile thus follows all Phase I tiles of its transform, which
+// is what makes the persistent launch deadlock-free.  len_index maps log2
+// length to the descriptor index stored in the items.
+static void schedule_items(const std::vector<int64_t> &lengths, const std::vector<long long> &off,
+                           const std::map<int, int> &len_index, long long lag, std::vector<BItem> &items,
+                           std::vector<int> &group)
+{
+    items.clear();
+    group.clear();
+    std::vector<int> order(lengths.size());
+    for (size_t i = 0; i < lengths.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return lengths[(size_t)x] > lengths[(size_t)y]; });
+    std::vector<BItem> small_items;
+    std::vector<int> big;
+    for (size_t k = 0; k < order.size();) {
+        const int i = order[k];
+        const int lg = ilog2_exact(lengths[(size_t)i]);
+        if (lg > batched::SMALL_MAX_LG) { big.push_back(i); ++k; continue; }
+        const int G = batched::ITEM >> lg;
+        BItem it;
+        memset(&it, 0, sizeof(it));
+        it.kind = 0;
+        it.len = len_index.at(lg);
+        it.a = (int)group.size();
+        int n = 0;
+        while (k < order.size() && n < G && ilog2_exact(lengths[(size_t)order[k]]) == lg) {
+            group.push_back(order[k]);
+            ++k; ++n;
+        }
+        it.b = n;
+        small_items.push_back(it);
+    }
+    auto ntiles = [&](int tr) { return (int)(lengths[(size_t)tr] / batched::ITEM); };
+    std::deque<std::pair<int, long long>> pending;  // (transform, earliest position)
+    auto emit_s2 = [&](int tr) {
+        const int li = len_index.at(ilog2_exact(lengths[(size_t)tr]));
+        for (int tl = 0; tl < ntiles(tr); ++tl) items.push_back(BItem{2, li, tr, tl, off[(size_t)tr], 0});
+    };
+    for (int tr : big) {
+        const int li = len_index.at(ilog2_exact(lengths[(size_t)tr]));
+        for (int tl = 0; tl < ntiles(tr); ++tl) items.push_back(BItem{1, li, tr, tl, off[(size_t)tr], 0});
+        pending.emplace_back(tr, (long long)items.size() + lag);
+        while (!pending.empty() && pending.front().second <= (long long)items.size()) {
+            emit_s2(pending.front().first);
+            pending.pop_front();
+        }
+    }
+    size_t si = 0;
+    while (!pending.empty() || si < small_items.size()) {
+        if (!pending.empty() && (pending.front().second <= (long long)items.size() || si == small_items.size())) {
+            emit_s2(pending.front().first);
+            pending.pop_front();
+        } else {
+            items.push_back(small_items[si++]);
+        }
+    }
+}
+
 // Builds the device tables, the length descriptors and the item order for
 // the current configuration.
 static paco_status_t build_device(paco_plan *pl, BatchedState *bs)
@@ -590,60 +653,9 @@ static paco_status_t build_device(paco_plan *pl, BatchedState *bs)
         lens.push_back(L);
     }
 
-    // transforms in decreasing length (stable), small ones grouped by length
-    std::vector<int> order((size_t)bs->count);
-    for (int64_t i = 0; i < bs->count; ++i) order[(size_t)i] = (int)i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int x, int y) { return bs->lengths[(size_t)x] > bs->lengths[(size_t)y]; });
     std::vector<BItem> items;
     std::vector<int> group;
-    std::vector<BItem> small_items;
-    std::vector<int> big;
-    for (size_t k = 0; k < order.size();) {
-        const int i = order[k];
-        const int lg = ilog2_exact(bs->lengths[(size_t)i]);
-        if (lg > batched::SMALL_MAX_LG) { big.push_back(i); ++k; continue; }
-        const int G = batched::ITEM >> lg;
-        BItem it;
-        memset(&it, 0, sizeof(it));
-        it.kind = 0;
-        it.len = len_index[lg];
-        it.a = (int)group.size();
-        int n = 0;
-        while (k < order.size() && n < G && ilog2_exact(bs->lengths[(size_t)order[k]]) == lg) {
-            group.push_back(order[k]);
-            ++k; ++n;
-        }
-        it.b = n;
-        small_items.push_back(it);
-    }
-    // Phase I tiles of the large transforms in order; a transform's Phase III
-    // tiles follow once `lag` more items have been queued after its last
-    // Phase I tile; small groups fill in at the end.
-    const long long lag = (long long)bs->lag_mult * bs->grid;
-    std::deque<std::pair<int, long long>> pending;  // (transform, earliest position)
-    auto emit_s2 = [&](int tr) {
-        const BLen &L = lens[(size_t)len_index[ilog2_exact(bs->lengths[(size_t)tr])]];
-        for (int tl = 0; tl < L.ntiles2; ++tl) items.push_back(BItem{2, len_index[L.lgN], tr, tl, bs->off[(size_t)tr], 0});
-    };
-    for (int tr : big) {
-        const int li = len_index[ilog2_exact(bs->lengths[(size_t)tr])];
-        for (int tl = 0; tl < lens[(size_t)li].ntiles1; ++tl) items.push_back(BItem{1, li, tr, tl, bs->off[(size_t)tr], 0});
-        pending.emplace_back(tr, (long long)items.size() + lag);
-        while (!pending.empty() && pending.front().second <= (long long)items.size()) {
-            emit_s2(pending.front().first);
-            pending.pop_front();
-        }
-    }
-    size_t si = 0;
-    while (!pending.empty() || si < small_items.size()) {
-        if (!pending.empty() && (pending.front().second <= (long long)items.size() || si == small_items.size())) {
-            emit_s2(pending.front().first);
-            pending.pop_front();
-        } else {
-            items.push_back(small_items[si++]);
-        }
-    }
+    schedule_items(bs->lengths, bs->off, len_index, (long long)bs->lag_mult * bs->grid, items, group);
     bs->nitems = (int)items.size();
 
     PACO_CUDA_TRY(cudaMalloc(&bs->d_items, std::max<size_t>(1, items.size()) * sizeof(BItem)));
@@ -956,4 +968,34 @@ extern "C" paco_status_t paco_plan_batched_config(const paco_plan_t *pl, int64_t
     if (ctas_per_sm) *ctas_per_sm = pl->bs->minb;
     if (lag) *lag = pl->bs->lag_mult;
     return PACO_OK;
+}
+
+extern "C" int64_t paco_debug_batched_schedule(const int64_t *lengths, int64_t count, int64_t lag_items,
+                                               int32_t *kind, int32_t *index, int32_t *tile, int64_t cap,
+                                               int32_t *group, int64_t group_cap)
+{
+    if (count < 0 || (count > 0 && !lengths) || lag_items < 0) return -1;
+    std::vector<int64_t> len((size_t)count);
+    std::vector<long long> off((size_t)count);
+    std::map<int, int> li;
+    long long tot = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int lg = ilog2_exact(lengths[i]);
+        if (lg < 4 || lg > 2 * batched::STAGE_MAX_LG) return -1;
+        len[(size_t)i] = lengths[i];
+        off[(size_t)i] = tot;
+        tot += lengths[i];
+        li[lg] = lg;
+    }
+    std::vector<BItem> items;
+    std::vector<int> grp;
+    schedule_items(len, off, li, lag_items, items, grp);
+    if ((int64_t)items.size() > cap || (int64_t)grp.size() > group_cap) return -1;
+    for (size_t k = 0; k < items.size(); ++k) {
+        kind[k] = items[k].kind;
+        index[k] = items[k].a;
+        tile[k] = items[k].b;
+    }
+    for (size_t k = 0; k < grp.size(); ++k) group[k] = grp[k];
+    return (int64_t)items.size();
 }
