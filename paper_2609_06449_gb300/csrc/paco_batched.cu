@@ -21,8 +21,13 @@
 //               finished Phase I tiles.  Items are ordered so that a
 //               transform's Phase III comes a fixed lag after its Phase I,
 //               long enough to avoid waiting and short enough for W to stay
-//               in L2 between the two (the HBM traffic is then ~16 B per
+//               in L2 between the two (at best 16 B of HBM traffic per
 //               element instead of 32).
+//
+// The plan's autotuner picks, per length, the N1 x N2 split and the radix b,
+// and for the whole batch the kernel variant (one or two CTAs per SM) and the
+// lag, by timing candidates at plan creation; it optimises time, so part of
+// the L2 residency can be traded for faster tiles.
 //
 // Deadlock freedom: only Phase III items wait, and only on Phase I items of
 // a lower queue index; those were claimed by running CTAs and never wait, so
