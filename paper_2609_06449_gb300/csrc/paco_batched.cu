@@ -126,6 +126,16 @@ __device__ __forceinline__ void small_group(const BatchedArgs &a, const BLen &ld
         for (int r = tid; r < (N >> LH); r += batched::NT) tw_hi[r] = tw[r << LH];
     }
     auto twid = [&](int r) { return cmul(tw_lo[r & ((1 << LH) - 1)], tw_hi[r >> LH]); };
+    // z^s, s < 16, for z = w_N^{-e}: from z, z^4, z^8 (three table reads)
+    // and at most two products, zh[s >> 2] * zl[s & 3]
+    auto powers = [&](C (&zl)[4], C (&zh)[4], int e) {
+        const C z1 = twid(e & (N - 1)), z4 = twid((4 * e) & (N - 1)), z8 = twid((8 * e) & (N - 1));
+        zl[0] = make_cx<float>(1.f, 0.f); zl[1] = z1; zl[2] = cmul(z1, z1); zl[3] = cmul(zl[2], z1);
+        zh[0] = make_cx<float>(1.f, 0.f); zh[1] = z4; zh[2] = z8; zh[3] = cmul(z8, z4);
+    };
+    auto zpow = [&](const C (&zl)[4], const C (&zh)[4], int s_) {
+        return ((s_ & 3) == 0) ? zh[s_ >> 2] : ((s_ >> 2) == 0) ? zl[s_ & 3] : cmul(zh[s_ >> 2], zl[s_ & 3]);
+    };
 
     for (int g = tid; g < gcount; g += batched::NT) s_off[g] = a.off[a.group_tx[gstart + g]];
     __syncthreads();
@@ -166,8 +176,10 @@ __device__ __forceinline__ void small_group(const BatchedArgs &a, const BLen &ld
         for (int r = 0; r < R1; ++r) v[q * R1 + r] = base[r * R2 * N2];
         dft<R1>(v + q * R1);
         if constexpr (R2 > 1) {
+            C zl[4], zh[4];
+            powers(zl, zh, jl * N2);                           // w_N1^{-jl} = w_N^{-jl N2}
 #pragma unroll
-            for (int s = 1; s < R1; ++s) v[q * R1 + s] = cmul(v[q * R1 + s], twid(s * jl * N2));
+            for (int s = 1; s < R1; ++s) v[q * R1 + s] = cmul(v[q * R1 + s], zpow(zl, zh, s));
 #pragma unroll
             for (int s = 0; s < R1; ++s) base[s * R2 * N2] = v[q * R1 + s];
         }
@@ -231,9 +243,11 @@ __device__ __forceinline__ void small_group(const BatchedArgs &a, const BLen &ld
         }
         dft<Q1>(v + q * Q1);
         if constexpr (Q2 > 1) {
+            C zl[4], zh[4];
+            powers(zl, zh, jl * N1);                           // w_N2^{-jl} = w_N^{-jl N1}
 #pragma unroll
             for (int s = 0; s < Q1; ++s) {
-                C y = (s > 0) ? cmul(v[q * Q1 + s], twid(s * jl * N1)) : v[q * Q1 + s];
+                C y = (s > 0) ? cmul(v[q * Q1 + s], zpow(zl, zh, s)) : v[q * Q1 + s];
                 const int j = s * Q2 + jl;
                 const int row = (int)digit_reverse((unsigned)j, LG2, t);
                 base[row * N1 + (col ^ (j & HM))] = y;
