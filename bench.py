@@ -496,13 +496,13 @@ def run_other(args, ranks, local):
         def step2(k=[0]):
             i = k[0] % K
             ev[i][0].record(stream)
-            plan.execute_stage1(x, y, -1, stream)
+            plan.execute_stage1(x, y, args.dir, stream)
             ev[i][1].record(stream)
-            plan.execute_stage2(y, y, -1, stream)
+            plan.execute_stage2(y, y, args.dir, stream)
             ev[i][2].record(stream)
             k[0] += 1
         for _ in range(W):
-            plan.execute(x, y, -1, stream)
+            plan.execute(x, y, args.dir, stream)
         tot, per, clocks = timed(step2)
         plan.check()
         s1 = statistics.mean(ev[k][0].elapsed_time(ev[k][1]) for k in range(K))
@@ -513,22 +513,23 @@ def run_other(args, ranks, local):
         dom_ms = max(s1, s2)
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
-        e2e = None if args.no_e2e else e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1), stream,
+        e2e = None if args.no_e2e else e2e_host(lambda: plan.execute_host(xh, ho, di, y, args.dir, stream), max(args.e2e_steps, 1), stream,
                        flop / 1e9, "GFLOP/s", N * 16, N * 16, "paco_execute_host (pinned host buffers)", mor,
                        world, ranks.barrier)
         hr = hbm_roofline("stage1" if s1 >= s2 else "stage2", 32.0 * N, dom_ms)
         import oracle
-        plan.execute(x, y, -1, stream)
+        plan.execute(x, y, args.dir, stream)
         torch.cuda.synchronize()
         ks = np.random.default_rng(5).integers(0, N, 8)
-        ref = oracle.dft_at(xh.numpy(), ks, threads=0)
+        ref = oracle.dft_at(xh.numpy(), ks, dir=args.dir, threads=0)
         got = y[torch.from_numpy(ks).cuda()].cpu().numpy()
         rms = math.sqrt(float((x.abs() ** 2).sum().item()))     # Parseval: rms of y = sqrt(sum |x|^2)
         acc = {"max_abs_err_over_rms": float(np.max(np.abs(got - ref)) / rms),
                "measured_on": "8 sampled coefficients vs the oracle's single-coefficient DFT"}
         line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s", higher_is_better=True,
                     ms_per_step=ms, dtype="f64",
-                    config={"workload": "c128 1-D DFT N=2^27 as N1=2^13 x N2=2^14, b=2, p=128, forward",
+                    config={"workload": "c128 1-D DFT N=2^27 as N1=2^13 x N2=2^14, b=2, p=128, "
+                                        + ("forward" if args.dir == -1 else "conjugate"), "dir": args.dir,
                             "N1": N1, "N2": N2, "b": 2, "p": 128, "batch": 1,
                             "input": "Re, Im i.i.d. U[-1,1), seed = rank", "l2": "inputs larger than L2"},
                     stage_ms={"stage1": s1, "stage2": s2}, hbm_gbs_effective=64.0 * N * world / (ms * 1e-3) / 1e9,
