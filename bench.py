@@ -15,7 +15,8 @@ Reported: 5 N log2 N GFLOP/s (whole job), effective HBM GB/s (32 N bytes per
 step: two reads and two writes of N complex64), the dominant kernel's
 roofline against the measured copy bandwidth, an end-to-end number through
 paco_execute_host with pinned host buffers, the CPU oracle on a bounded
-sample, and SM clocks sampled during the timed region.
+sample, SM clocks sampled during the timed region, and cuFFT on the same
+input as context.
 
 Other workloads (--workload): A (2^16 as 256 x 256, latency), B128
 (complex128 N = 2^27), C (the uneven batch in one persistent launch), D
@@ -25,7 +26,7 @@ paco_permute -> Phase III on the headline transform: the ablation of the
 fused redistribution).  Each prints one line of the same contract.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paco|reference]
-                  [--workload B|A|B128|C|D|E]
+                  [--workload B|A|B128|C|D|E|U] [--dir -1|1]
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 transform does not shard across GPUs on this path); timing is the max over
