@@ -120,7 +120,7 @@ paco_plan_t *paco_plan_create(int64_t N1, int64_t N2, int b, int64_t batch,
                               paco_dtype_t dtype);
 
 /* paco_plan_create_ex -- as paco_plan_create with explicit options (p, tile,
- * cluster).  p must be a power of b with p >= 2, p | N1 and p | N2
+ * cluster, CTAs per SM).  p must be a power of b with p >= 2, p | N1 and p | N2
  * (Eq. exact-divisibility).  Writes the plan to *out (NULL on error). */
 paco_status_t paco_plan_create_ex(paco_plan_t **out, const paco_plan_opts_t *opts);
 
@@ -140,7 +140,10 @@ paco_status_t paco_plan_info(const paco_plan_t *plan, paco_plan_info_t *info);
  * buffers of batch*N elements of the plan's dtype; `out` also holds the
  * intermediate W = Z-hat (Eq. (17)) between the two kernels, so no scratch
  * is used.  in == out, or overlapping buffers, return PACO_ERR_ALIASING.
- * batch = 0 is a no-op.  Asynchronous on `stream`.
+ * batch = 0 is a no-op.  Asynchronous on `stream`.  Executions of one plan
+ * must not overlap in time (a plan with a 2^14 complex64 factor, and an
+ * uneven-batch plan, run pipelines whose ring buffers and counters the plan
+ * owns): use one plan per concurrently used stream.
  */
 paco_status_t paco_execute(paco_plan_t *plan, const void *in, void *out, int dir,
                            paco_stream_t stream);
