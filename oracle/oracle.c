@@ -103,21 +103,13 @@ int oracle_dft_direct(int64_t n, const double *x, double *y, int dir)
 /* ---------------------------------------------------------------------- */
 /* Recursive radix-2 decimation-in-time FFT (textbook Cooley-Tukey).       */
 /* ---------------------------------------------------------------------- */
-/* y[0..n) = DFT_n of x[0], x[stride], ..., x[(n-1)*stride].
- * tw[r] = w_N^{dir*r} for r < N/2; at size n the needed root w_n^{dir*k}
- * equals tw[k * (N/n)], i.e. stride tw_step = N/n.                        */
-static void fft_rec(int64_t n, const double *x, int64_t stride, double *y,
-                    const double *tw, int64_t tw_step)
+/* The butterflies of one combine step, k in [k0, k1): y[k], y[k+h] from the
+ * half-length DFTs of the evens (y[0..h)) and the odds (y[h..n)).
+ * tw[r] = w_N^{dir*r} for r < N/2; at size n = 2h the root w_n^{dir*k}
+ * is tw[k * tw_step] with tw_step = N/n.                                  */
+static void combine(int64_t h, double *y, const double *tw, int64_t tw_step, int64_t k0, int64_t k1)
 {
-    if (n == 1) {
-        y[0] = x[0];
-        y[1] = x[1];
-        return;
-    }
-    int64_t h = n / 2;
-    fft_rec(h, x, 2 * stride, y, tw, 2 * tw_step);                /* evens */
-    fft_rec(h, x + 2 * stride, 2 * stride, y + 2 * h, tw, 2 * tw_step); /* odds */
-    for (int64_t k = 0; k < h; ++k) {
+    for (int64_t k = k0; k < k1; ++k) {
         int64_t ti_ = (ORACLE_PLANT == 3) ? k : k * tw_step;
         double wr = tw[2 * ti_], wi = tw[2 * ti_ + 1];
         if (ORACLE_PLANT == 1) wi = -wi;
@@ -133,11 +125,68 @@ static void fft_rec(int64_t n, const double *x, int64_t stride, double *y,
     }
 }
 
+/* y[0..n) = DFT_n of x[0], x[stride], ..., x[(n-1)*stride].               */
+static void fft_rec(int64_t n, const double *x, int64_t stride, double *y,
+                    const double *tw, int64_t tw_step)
+{
+    if (n == 1) {
+        y[0] = x[0];
+        y[1] = x[1];
+        return;
+    }
+    int64_t h = n / 2;
+    fft_rec(h, x, 2 * stride, y, tw, 2 * tw_step);                /* evens */
+    fft_rec(h, x + 2 * stride, 2 * stride, y + 2 * h, tw, 2 * tw_step); /* odds */
+    combine(h, y, tw, tw_step, 0, h);
+}
+
+/* The same recursion with its top `depth` levels spread over OpenMP tasks:
+ * the two halves of a level run as two tasks, and its combine step is cut
+ * into independent ranges of k.  Every output is produced by the same
+ * butterflies, on the same operands, as in fft_rec, so the result is
+ * bit-identical to the serial one for any thread count.  Called from inside
+ * a parallel region.                                                      */
+static void fft_rec_tasks(int64_t n, const double *x, int64_t stride, double *y,
+                          const double *tw, int64_t tw_step, int depth)
+{
+    if (depth <= 0 || n < ((int64_t)1 << 15)) {
+        fft_rec(n, x, stride, y, tw, tw_step);
+        return;
+    }
+    int64_t h = n / 2;
+#ifdef _OPENMP
+#pragma omp task
+#endif
+    fft_rec_tasks(h, x, 2 * stride, y, tw, 2 * tw_step, depth - 1);
+#ifdef _OPENMP
+#pragma omp task
+#endif
+    fft_rec_tasks(h, x + 2 * stride, 2 * stride, y + 2 * h, tw, 2 * tw_step, depth - 1);
+#ifdef _OPENMP
+#pragma omp taskwait
+#endif
+    const int64_t chunk = (int64_t)1 << 14;
+    for (int64_t k0 = 0; k0 < h; k0 += chunk) {
+        int64_t k1 = k0 + chunk < h ? k0 + chunk : h;
+#ifdef _OPENMP
+#pragma omp task firstprivate(k0, k1)
+#endif
+        combine(h, y, tw, tw_step, k0, k1);
+    }
+#ifdef _OPENMP
+#pragma omp taskwait
+#endif
+}
+
 static double *make_half_table(int64_t n, int dir)
 {
     int64_t h = n > 1 ? n / 2 : 1;
     double *tw = (double *)malloc(sizeof(double) * 2 * (size_t)h);
     if (!tw) return NULL;
+    /* each entry depends on r alone: the loop may run on any thread count */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) if (h >= 65536)
+#endif
     for (int64_t r = 0; r < h; ++r) {
         long double c, s;
         unit_root_ld(r, n, dir, &c, &s);
@@ -147,9 +196,12 @@ static double *make_half_table(int64_t n, int dir)
     return tw;
 }
 
-/* Batched recursive FFT: `batch` contiguous transforms of length n.
- * Transforms of one batch run in parallel over up to `threads` OpenMP
- * threads (threads <= 0: the runtime default).                           */
+/* Batched recursive FFT: `batch` contiguous transforms of length n, on up
+ * to `threads` OpenMP threads (threads <= 0: the runtime default).  With at
+ * least as many transforms as threads, whole transforms run in parallel;
+ * otherwise each transform's top recursion levels run as tasks
+ * (fft_rec_tasks).  Either way each output comes from the same arithmetic
+ * as the one-thread recursion.                                            */
 int oracle_fft(int64_t n, int64_t batch, const double *x, double *y, int dir, int threads)
 {
     if (!is_pow2(n) || batch < 0 || (dir != -1 && dir != 1)) return -1;
@@ -158,10 +210,23 @@ int oracle_fft(int64_t n, int64_t batch, const double *x, double *y, int dir, in
     if (!tw) return -2;
 #ifdef _OPENMP
     int nt = threads > 0 ? threads : omp_get_max_threads();
+    if (batch >= nt || nt == 1) {
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt) if (batch > 1)
-#endif
+        for (int64_t t = 0; t < batch; ++t)
+            fft_rec(n, x + 2 * t * n, 1, y + 2 * t * n, tw, 1);
+    } else {
+        int depth = 0;
+        while ((1 << depth) < 4 * nt) ++depth;     /* about four tasks per thread */
+        for (int64_t t = 0; t < batch; ++t) {
+#pragma omp parallel num_threads(nt)
+#pragma omp single
+            fft_rec_tasks(n, x + 2 * t * n, 1, y + 2 * t * n, tw, 1, depth);
+        }
+    }
+#else
     for (int64_t t = 0; t < batch; ++t)
         fft_rec(n, x + 2 * t * n, 1, y + 2 * t * n, tw, 1);
+#endif
     (void)threads;
     free(tw);
     return 0;

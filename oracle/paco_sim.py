@@ -199,20 +199,26 @@ def fused_macro_digit_reversal(X: np.ndarray, b: int, g) -> None:
 
 
 def para_co_drp(slabs, N1: int, N2: int, b: int, p: int, dir: int = -1,
-                twiddle: bool = True, trace=None):
+                twiddle: bool = True, trace=None, plant: str | None = None):
     """Run the middle stage on p simulated processors.
 
     ``slabs[q]`` is processor q's Phase-I slab X_q (N1 x N2/p).  Returns the
     list of target slabs Y_q (N2 x N1/p).  With ``twiddle=False`` the data are
     moved only (for label-tracing).  ``trace``, if a dict, receives the packed
-    slabs, the blocks sent per (q, q'), and the raw received regions."""
+    slabs, the blocks sent per (q, q'), and the raw received regions.
+    ``plant`` exists only so that the tests can show their pins catching a
+    plausible mistake: ``"route_by_a"`` skips the local pack's digit reversal,
+    so the row block sent to q' is chosen by the physical row a instead of
+    the frequency pi_m1(a) it holds."""
     N = N1 * N2
     w1, w2 = N1 // p, N2 // p                  # N1/p and N2/p
     packed = []
     sent = {}
     for q in range(p):
         Xq = np.array(slabs[q], copy=True)
-        if twiddle:
+        if plant == "route_by_a":
+            pass
+        elif twiddle:
             c = q * w2 + np.arange(w2)         # global column of each c_loc
             Xq = Xq.astype(np.complex128)
             fused_macro_digit_reversal(Xq, b, lambda v: root(v * c, N, dir))
@@ -290,15 +296,35 @@ def simulate(x, N1: int, N2: int, b: int, p: int, dir: int = -1,
     return {"A_tilde": A_t, "W": W, "slabs": out, "Y": Y, "m1": m1, "m2": m2}
 
 
-def balance_counts(N1: int, N2: int, b: int, p: int) -> np.ndarray:
-    """counts[q, q'] = number of items that PARA-CO-DRP routes from source q
-    to destination q', found by running the procedure on labels."""
-    labels = np.arange(N1 * N2, dtype=np.int64).reshape(N1, N2)
+def balance_counts(N1: int, N2: int, b: int, p: int, plant: str | None = None) -> np.ndarray:
+    """counts[q, q'] = number of items that PARA-CO-DRP sends from processor q
+    to processor q' AND that belong on that route by their own coordinates.
+
+    Every item is labelled with its Phase-I position (a, c).  Its source is
+    the input owner of column c, q = floor(c / (N2/p)) (Sect. 2, input
+    ownership), and its destination is the owner of the output column it
+    feeds, k1 = pi_m1(a) (the frequency that physical row a holds after
+    Phase I, Lemma 1), q' = floor(pi_m1(a) / (N1/p)) (Eq. (3)).  The
+    procedure runs on the labels and every label found in a block it sends
+    from q to q' is counted only if its coordinates give that same (q, q').
+    Theorem 4 then fixes counts == N/p^2 everywhere; a misrouted item lowers
+    some count.  Raises if a label is sent twice or never."""
+    import oracle
+    N = N1 * N2
+    labels = np.arange(N, dtype=np.int64).reshape(N1, N2)   # label = a*N2 + c
     trace = {}
-    w2 = N2 // p
+    w1, w2 = N1 // p, N2 // p
     slabs = [labels[:, q * w2:(q + 1) * w2] for q in range(p)]
-    para_co_drp(slabs, N1, N2, b, p, twiddle=False, trace=trace)
+    para_co_drp(slabs, N1, N2, b, p, twiddle=False, trace=trace, plant=plant)
+    pi1 = oracle.digit_reverse_table(b, log_b(N1, b))
     counts = np.zeros((p, p), dtype=np.int64)
+    seen = np.zeros(N, dtype=np.int64)
     for (q, qd), blk in trace["sent"].items():
-        counts[q, qd] = blk.size
+        lab = np.asarray(blk, dtype=np.int64).ravel()
+        np.add.at(seen, lab, 1)
+        a, c = lab // N2, lab % N2
+        ok = (c // w2 == q) & (pi1[a] // w1 == qd)
+        counts[q, qd] += int(np.count_nonzero(ok))
+    if not np.all(seen == 1):
+        raise AssertionError("an item was sent more than once or never")
     return counts

@@ -8,7 +8,9 @@
    sends every destination its (N1/p) x (N2/p) block over gloo point-to-point
    (one balanced exchange: N/p^2 items per ordered pair, the self block stays
    local), transposes the received blocks and unpacks.  The result must equal
-   the single-process procedure and the closed form Z-hat of Eq. (17)."""
+   the single-process procedure and the closed form Z-hat of Eq. (17); the
+   items' labels travel the same exchange, and each receiving rank counts, per
+   source, the items whose own coordinates route them to it (N/p^2 each)."""
 
 import os
 import socket
@@ -80,23 +82,39 @@ def _drp_worker(rank, p, port, N1, N2, b, q):
     Xq = np.array(A_t[:, rank * w2:(rank + 1) * w2])                 # this processor's slab
     c = rank * w2 + np.arange(w2)
     ps.fused_macro_digit_reversal(Xq, b, lambda v: ps.root(v * c, N, -1))   # local pack
-    recv = {}
-    reqs, bufs = [], {}
-    for qd in range(p):                                               # one balanced exchange
-        blk = np.ascontiguousarray(Xq[qd * w1:(qd + 1) * w1, :])
-        if qd == rank:
-            recv[rank] = blk                                          # self block stays local
-            continue
-        t = torch.from_numpy(blk.view(np.float64).copy())
-        reqs.append(dist.isend(t, dst=qd))
-        r = torch.empty_like(t)
-        bufs[qd] = r
-        reqs.append(dist.irecv(r, src=qd))
-    for rq in reqs:
-        rq.wait()
-    for qd, r in bufs.items():
-        recv[qd] = r.numpy().view(np.complex128).reshape(w1, w2)
-    sizes = {qd: recv[qd].size for qd in recv}
+    # the labels a*N2 + c of this slab's items, packed by the same reversal
+    # (the pack moves whole rows; the fused twiddle does not move anything)
+    lab = (np.arange(N1)[:, None] * N2 + rank * w2 + np.arange(w2)[None, :]).astype(np.int64)
+    ps.macro_digit_reversal(lab, b)
+
+    def exchange(arr, np_dtype, view):
+        recv, reqs, bufs = {}, [], {}
+        for qd in range(p):                                           # one balanced exchange
+            blk = np.ascontiguousarray(arr[qd * w1:(qd + 1) * w1, :])
+            if qd == rank:
+                recv[rank] = blk                                      # self block stays local
+                continue
+            t = torch.from_numpy(blk.view(view).copy())
+            reqs.append(dist.isend(t, dst=qd))
+            r = torch.empty_like(t)
+            bufs[qd] = r
+            reqs.append(dist.irecv(r, src=qd))
+        for rq in reqs:
+            rq.wait()
+        for qd, r in bufs.items():
+            recv[qd] = r.numpy().view(np_dtype).reshape(w1, w2)
+        return recv
+
+    recv = exchange(Xq, np.complex128, np.float64)
+    rlab = exchange(lab, np.int64, np.int64)
+    # items received from each source whose own coordinates route them here:
+    # source = owner of input column c, destination = owner of k1 = pi_m1(a)
+    import oracle
+    pi1 = oracle.digit_reverse_table(b, ps.log_b(N1, b))
+    sizes = {}
+    for src, L in rlab.items():
+        a, c = L // N2, L % N2
+        sizes[src] = int(np.count_nonzero((c // w2 == src) & (pi1[a] // w1 == rank)))
     Yq = np.empty((N2, w1), dtype=np.complex128)
     for src in range(p):                                              # per-block transpose
         Yq[src * w2:(src + 1) * w2, :] = recv[src].T
@@ -127,8 +145,10 @@ def test_para_co_drp_over_gloo(N1, N2, b, p):
     N = N1 * N2
     x = gaussian(N, 21, np.complex128)
     single = ps.simulate(x, N1, N2, b, p, phase1="lemma")
-    # exactly N/p^2 items per ordered pair (Theorem 4)
+    # exactly N/p^2 correctly routed items per ordered pair (Theorem 4),
+    # counted on the receiving rank by the items' own coordinates
     for rank in range(p):
+        assert sorted(res[rank][1]) == list(range(p))
         assert all(v == N // (p * p) for v in res[rank][1].values())
     W = np.concatenate([res[r][0] for r in range(p)], axis=1)
     assert np.allclose(W, single["W"], atol=1e-12)

@@ -111,3 +111,16 @@ def test_bad_arguments_are_rejected():
         oracle.fft(np.zeros(12, complex))          # not a power of two
     with pytest.raises(ValueError):
         oracle.dft_at(np.zeros(8, complex), [8])   # k out of range
+
+
+@pytest.mark.parametrize("lg,batch", [(15, 1), (18, 1), (17, 3), (16, 16)])
+@pytest.mark.parametrize("d", [-1, 1])
+def test_threaded_fft_is_bit_identical(lg, batch, d):
+    """The OpenMP forms (top recursion levels as tasks for a few large
+    transforms, whole transforms per thread for many) run the same butterflies
+    on the same operands as the one-thread recursion: the outputs must be
+    equal bit for bit, whatever the thread count."""
+    x = uniform(batch << lg, 5, np.complex128).reshape(batch, 1 << lg)
+    one = oracle.fft(x, dir=d, threads=1)
+    for t in (2, 3, 8):
+        assert np.array_equal(oracle.fft(x, dir=d, threads=t), one)

@@ -86,14 +86,31 @@ def test_coordinate_trace(N1, N2, b, p):
 
 @pytest.mark.parametrize("N1,N2,b,p", CONFIGS)
 def test_balance_counts(N1, N2, b, p):
-    """Theorem 4: exactly N/p^2 items per ordered pair; h = (N/p)(1 - 1/p),
-    mu = N(1 - 1/p)."""
+    """Theorem 4: exactly N/p^2 items per ordered pair, N/p staying on the
+    diagonal (self pairs), h = (N/p)(1 - 1/p) sent by each processor and
+    mu = N(1 - 1/p) in all -- counting only the items whose own coordinates
+    (source = owner of input column c, destination = owner of output column
+    pi_m1(a)) match the route the procedure sent them on."""
     N = N1 * N2
     counts = ps.balance_counts(N1, N2, b, p)
     assert np.all(counts == N // (p * p))
+    assert np.all(np.diag(counts) == N // (p * p))
+    assert counts.sum() == N                          # every item routed where it belongs
+    assert np.all(counts.sum(axis=1) == N // p)       # each processor's slab leaves once
     remote = counts.sum() - np.trace(counts)
     assert remote == N - N // p                       # mu
     assert np.all(counts.sum(axis=1) - np.diag(counts) == N // p - N // (p * p))   # h
+
+
+@pytest.mark.parametrize("N1,N2,b,p", CONFIGS)
+def test_balance_pin_catches_misrouting(N1, N2, b, p):
+    """A planted mistake in the simulator -- row blocks chosen by the physical
+    row a instead of the frequency pi_m1(a) it holds (no local pack
+    reversal) -- must break the balance pin: some items then travel to a
+    processor that does not own their output column."""
+    N = N1 * N2
+    counts = ps.balance_counts(N1, N2, b, p, plant="route_by_a")
+    assert not np.all(counts == N // (p * p))
 
 
 @pytest.mark.parametrize("N1,N2,b,p", [(16, 16, 2, 2), (64, 16, 4, 4), (16, 64, 4, 4),
