@@ -311,11 +311,35 @@ int64_t paco_debug_batched_schedule(const int64_t *lengths, int64_t count, int64
  * twiddle tables (synchronously); make it before any stream capture.  Later
  * calls only enqueue work on `stream`.  All calls on one device share the
  * arrays and each leaves its intermediates there: calls whose work overlaps on
- * the GPU race and must be ordered by the caller.  Errors are reported as for
- * the other entry points (paco_last_error()).
+ * the GPU race and must be ordered by the caller.  Argument and launch errors
+ * are returned by the call (message from paco_last_error()); errors raised
+ * while its kernels run (a bounded wait that gave up) are recorded in the
+ * library's status word on the device and returned by the next
+ * paco_noalloc_check() on that device.
  */
 paco_status_t paco_execute_noalloc(const void *in, void *out, int b, int64_t batch, int dir,
                                    paco_stream_t stream);
+
+/*
+ * paco_noalloc_check -- the device-side status of paco_execute_noalloc on
+ * the current device: synchronises the device, reads and clears the status
+ * word the kernels write, and returns PACO_OK, PACO_ERR_TIMEOUT (a bounded
+ * wait gave up: the output of the call that raised it is not valid) or
+ * PACO_ERR_DEVICE; PACO_ERR_CUDA if the device cannot be read.  Allocates
+ * nothing.  PACO_OK when paco_execute_noalloc has not run on the device.
+ */
+paco_status_t paco_noalloc_check(void);
+
+/*
+ * paco_debug_noalloc_set_waits -- test hook for the bounded waits of
+ * paco_execute_noalloc, as paco_debug_set_waits is for a plan (the paper has
+ * no counterpart): spin_limit replaces the default poll limit (0 restores
+ * it), wait_bias is added to every dependency target, so with wait_bias > 0
+ * the next call's waits give up and paco_noalloc_check reports
+ * PACO_ERR_TIMEOUT while the CUDA context stays usable.  Applies to calls
+ * made after it, on every device.  Set both to 0 for normal use.
+ */
+void paco_debug_noalloc_set_waits(unsigned spin_limit, unsigned wait_bias);
 
 #ifdef __cplusplus
 }

@@ -124,6 +124,10 @@ def _load():
     L.paco_debug_set_waits.restype = i32
     L.paco_execute_noalloc.argtypes = [vp, vp, i32, i64, i32, vp]
     L.paco_execute_noalloc.restype = i32
+    L.paco_noalloc_check.argtypes = []
+    L.paco_noalloc_check.restype = i32
+    L.paco_debug_noalloc_set_waits.argtypes = [ctypes.c_uint, ctypes.c_uint]
+    L.paco_debug_noalloc_set_waits.restype = None
     return L
 
 
@@ -139,6 +143,12 @@ def execute_noalloc(x, out, b: int, batch: int, dir: int = -1, stream=None) -> N
     """paco_execute_noalloc: the N1 = N2 = 2^14 complex64 transform without
     any allocation (the library's reserved device arrays); see paco.h."""
     _check(lib.paco_execute_noalloc(_ptr(x), _ptr(out), int(b), int(batch), int(dir), _stream(stream)))
+
+
+def noalloc_check() -> None:
+    """paco_noalloc_check: raise if a kernel of paco_execute_noalloc on the
+    current device recorded an error (e.g. a bounded wait that gave up)."""
+    _check(lib.paco_noalloc_check())
 
 
 def digit_reverse(u: int, b: int, ell: int) -> int:
@@ -277,10 +287,18 @@ def _dtype_code(t) -> int:
 
 
 def get_plan(N1: int, N2: int, b: int, batch: int, dtype: int, p: int = 0,
-             device: int | None = None) -> Plan:
+             device: int | None = None, stream: int | None = None) -> Plan:
+    """The cached plan for this shape on ``device`` and ``stream``.
+
+    A plan's executions must not overlap in time (the 2^14 complex64 panel
+    pipeline keeps its ring buffers and counters in the plan), so plans are
+    cached per stream: calls on one stream are ordered by that stream, and
+    calls on different streams get different plans."""
     import torch
     dev = torch.cuda.current_device() if device is None else device
-    key = (N1, N2, b, batch, dtype, p, dev)
+    if stream is None:
+        stream = int(torch.cuda.current_stream(dev).cuda_stream)
+    key = (N1, N2, b, batch, dtype, p, dev, int(stream))
     pl = _PLANS.get(key)
     if pl is None:
         with torch.cuda.device(dev):
@@ -293,7 +311,8 @@ def fft(x, N1: int, N2: int, b: int, p: int = 0, dir: int = -1, out=None):
     """PACO transform of the last dimension of ``x`` (length N1*N2) for every
     leading index: dir=-1 the paper's forward DFT, dir=+1 the unnormalised
     conjugate transform.  ``x`` must be a contiguous complex64/complex128 CUDA
-    tensor; returns a new tensor (or fills ``out``)."""
+    tensor; returns a new tensor (or fills ``out``).  The work is enqueued on
+    the current stream of ``x``'s device, with a plan cached for that stream."""
     import torch
     if not x.is_cuda:
         raise ValueError("PACO runs on the GPU: x must be a CUDA tensor")
@@ -304,8 +323,13 @@ def fft(x, N1: int, N2: int, b: int, p: int = 0, dir: int = -1, out=None):
     batch = x.numel() // N
     if out is None:
         out = torch.empty_like(x)
-    pl = get_plan(int(N1), int(N2), int(b), batch, _dtype_code(x), int(p), x.device.index)
-    pl.execute(x, out, dir)
+    elif out.device != x.device:
+        raise ValueError("out must be on the device of x")
+    dev = x.device.index
+    stream = int(torch.cuda.current_stream(x.device).cuda_stream)
+    with torch.cuda.device(dev):
+        pl = get_plan(int(N1), int(N2), int(b), batch, _dtype_code(x), int(p), dev, stream)
+        pl.execute(x, out, dir, stream)
     return out
 
 

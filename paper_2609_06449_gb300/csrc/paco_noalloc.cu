@@ -46,6 +46,10 @@ constexpr int kP = 64;                                   // panel width (columns
 constexpr long long kPanelsPerBatch = kL / kP;           // 256
 constexpr long long kScratchElems = (long long)panel::NBUF * kL * kP;   // 3 * 2^20
 constexpr int kCtrWords = (int)(2 * PACO_NOALLOC_MAX_BATCH * kPanelsPerBatch + 1);
+// a stage clears and uses 2 * batch * panels + 1 counter words (queue, A and
+// B completions per panel): the largest accepted batch must fit
+static_assert(2LL * PACO_NOALLOC_MAX_BATCH * kPanelsPerBatch + 1 <= (long long)kCtrWords,
+              "counter array too small for PACO_NOALLOC_MAX_BATCH");
 
 __device__ __align__(256) float2 g_scratch[kScratchElems];   // 24 MiB panel ring
 __device__ __align__(256) unsigned g_ctr[kCtrWords];         // queue + per-panel counters
@@ -79,6 +83,10 @@ struct DeviceState {
 constexpr int kMaxDevices = 64;
 DeviceState g_state[kMaxDevices];
 std::mutex g_mutex;
+
+// paco_debug_noalloc_set_waits: poll limit (0 = default) and the bias added
+// to every dependency target of the bounded waits
+unsigned g_dbg_spin_limit = 0, g_dbg_wait_bias = 0;
 
 paco_status_t fail(paco_status_t st, const char *msg)
 {
@@ -176,7 +184,8 @@ bool stage_args(const DeviceState &s, int mode, int b, int t, long long batch, c
     a->twN_lo_bits = kLg;
     a->N_mask = (unsigned)(kN - 1);
     a->conj = (dir == 1);
-    a->spin_limit = 1u << 22;
+    a->spin_limit = g_dbg_spin_limit ? g_dbg_spin_limit : 1u << 22;
+    a->dep_bias = g_dbg_wait_bias;
     if (mode == 1) {
         const cuuint64_t dims[4] = {(cuuint64_t)kL, 128, 128, (cuuint64_t)batch};
         const cuuint64_t str[3] = {(cuuint64_t)kL * E, (cuuint64_t)kL * 128 * E, (cuuint64_t)kN * E};
@@ -265,4 +274,34 @@ extern "C" paco_status_t paco_execute_noalloc(const void *in, void *out, int b, 
             return fail(PACO_ERR_CUDA, "paco_execute_noalloc: launch failed");
     }
     return PACO_OK;
+}
+
+extern "C" paco_status_t paco_noalloc_check(void)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail(PACO_ERR_CUDA, "paco_noalloc_check: no current device");
+    int *status = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_mutex);
+        if (!g_state[dev].ready) return PACO_OK;          // nothing has run on this device
+        status = g_state[dev].status;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess)
+        return fail(PACO_ERR_CUDA, "paco_noalloc_check: device synchronisation failed");
+    int h = 0;
+    if (cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemset(status, 0, sizeof(int)) != cudaSuccess)
+        return fail(PACO_ERR_CUDA, "paco_noalloc_check: status word read failed");
+    if (h == PACO_ERR_TIMEOUT)
+        return fail(PACO_ERR_TIMEOUT, "paco_execute_noalloc: a bounded device wait gave up");
+    if (h != 0) return fail(PACO_ERR_DEVICE, "paco_execute_noalloc: a device-side check set the status word");
+    return PACO_OK;
+}
+
+extern "C" void paco_debug_noalloc_set_waits(unsigned spin_limit, unsigned wait_bias)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    g_dbg_spin_limit = spin_limit;
+    g_dbg_wait_bias = wait_bias;
 }

@@ -7,8 +7,10 @@ library offers one entry point that runs the N1 = N2 = 2^14 complex64
 transform entirely out of device arrays it reserves when it is loaded.  This
 file calls it through the C ABI twice in a row, on different inputs, and
 compares each result with the plan-based paco_execute within the tolerance
-of the parity tests (relative L2 error <= 5e-7 * log2 N).  It sits last in
-collection order so that a failure here stops a `-x` run only after every
+of the parity tests (relative L2 error <= 5e-7 * log2 N); runs the b = 2
+layout with batch = 2 against paco_execute and the FP64 oracle; and checks
+that a device-side timeout is reported by paco_noalloc_check().  It sits last
+in collection order so that a failure here stops a `-x` run only after every
 other test has run."""
 
 import ctypes
@@ -58,6 +60,66 @@ def test_noalloc_matches_paco_execute_twice():
         err = _rel(got, ref)
         assert err <= TOL, f"call {call}: rel L2 vs paco_execute {err:.3e} > {TOL:.3e}"
         del x
+    torch.cuda.empty_cache()
+
+
+def test_noalloc_b2_batch2_matches_plan_and_oracle():
+    """The b = 2 layout (a different run structure of the digit-reversed rows
+    that stage 2 reads) with batch = 2 (the batch folded into the last tensor
+    dimension, twice the counters): element-wise against paco_execute on a
+    b = 2, batch = 2 plan and, per transform, against the FP64 oracle."""
+    import oracle
+    batch = 2
+    xh = np.stack([uniform(N, 31, np.complex64), gaussian(N, 32, np.complex64)])
+    x = torch.from_numpy(xh).cuda()
+    got = torch.full_like(x, float("nan"))
+    plan = paco.Plan(N1, N2, 2, batch, paco.C64, p=128)
+    ref = torch.empty_like(x)
+    for d in (-1, +1):
+        rc = _noalloc(x, got, 2, batch, d)
+        assert rc == 0, paco.lib.paco_last_error().decode()
+        plan.execute(x, ref, d)
+        torch.cuda.synchronize()
+        assert paco.lib.paco_noalloc_check() == 0
+        for t in range(batch):
+            err = _rel(got[t], ref[t])
+            assert err <= TOL, f"dir {d} transform {t}: rel L2 vs paco_execute {err:.3e}"
+        gh = got.cpu().numpy()
+        for t in range(batch):
+            want = oracle.fft(xh[t].astype(np.complex128).reshape(1, -1), dir=d).ravel()
+            err = np.linalg.norm(gh[t].astype(np.complex128) - want) / np.linalg.norm(want)
+            assert err <= TOL, f"dir {d} transform {t}: rel L2 vs oracle {err:.3e} > {TOL:.3e}"
+            del want
+    del x, got, ref
+    torch.cuda.empty_cache()
+
+
+def test_noalloc_reports_a_forced_timeout():
+    """A bounded wait that gives up inside paco_execute_noalloc is reported by
+    the next paco_noalloc_check() (PACO_ERR_TIMEOUT); the check clears it, the
+    context stays usable and the next normal call is correct.  The timeout is
+    forced with the test hook: a short poll limit and a dependency target no
+    counter reaches, so every wait ends by itself."""
+    x = torch.from_numpy(uniform(N, 41, np.complex64)).cuda()
+    got = torch.empty_like(x)
+    assert paco.lib.paco_noalloc_check() == 0                 # nothing pending
+    paco.lib.paco_debug_noalloc_set_waits(2000, 1 << 20)
+    try:
+        assert _noalloc(x, got, 4, 1) == 0                    # enqueued fine
+        torch.cuda.synchronize()
+        assert paco.lib.paco_noalloc_check() == 5             # PACO_ERR_TIMEOUT
+        assert b"bounded" in paco.lib.paco_last_error()
+    finally:
+        paco.lib.paco_debug_noalloc_set_waits(0, 0)
+    assert paco.lib.paco_noalloc_check() == 0                 # cleared by the check
+    assert _noalloc(x, got, 4, 1) == 0
+    plan = paco.Plan(N1, N2, 4, 1, paco.C64, p=64)
+    ref = torch.empty_like(x)
+    plan.execute(x, ref, -1)
+    torch.cuda.synchronize()
+    assert paco.lib.paco_noalloc_check() == 0
+    assert _rel(got, ref) <= TOL
+    del x, got, ref
     torch.cuda.empty_cache()
 
 
