@@ -146,9 +146,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_sample(lg: int, seconds: float, dtype: str):
+def oracle_sample(lg: int, seconds: float, dtype: str, threads: int = 1):
     """Time the CPU oracle (FP64 recursive FFT, as it stands) on one 2^lg
-    transform of the same recipe, repeated until `seconds` of work."""
+    transform of the same recipe, repeated until `seconds` of work, on
+    `threads` OpenMP threads (its top recursion levels run as tasks)."""
     import numpy as np
 
     import oracle
@@ -160,12 +161,20 @@ def oracle_sample(lg: int, seconds: float, dtype: str):
     reps, total = 0, 0.0
     while total < seconds or reps == 0:
         t = time.perf_counter()
-        oracle.fft(x, threads=1)
+        oracle.fft(x, threads=threads)
         total += time.perf_counter() - t
         reps += 1
     per = total / reps
     gflops = 5.0 * n * lg / per / 1e9
     return gflops, per, reps
+
+
+def host_cores() -> int:
+    """The host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover - non-Linux
+        return os.cpu_count() or 1
 
 
 def run_reference(args, rank: int, world: int):
@@ -182,24 +191,25 @@ def run_reference(args, rank: int, world: int):
     from paco_inputs import uniform
 
     n = 1 << lg
+    cores = host_cores()
     x = uniform(n, 0, np.complex64).astype(np.complex128)
     for _ in range(max(args.warmup, 0)):
-        oracle.fft(x, threads=1)
+        oracle.fft(x, threads=cores)
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle.fft(x, threads=1)
+        oracle.fft(x, threads=cores)
     el = time.perf_counter() - t
     per = el / max(args.steps, 1)
     v = 5.0 * n * lg / per / 1e9
     sample = (f"one 2^{lg}-point transform per step (same U[-1,1) recipe, seed 0), "
-              f"FP64 recursive radix-2 oracle, 1 thread")
+              f"FP64 recursive radix-2 oracle, {cores} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(args),
-        "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -322,34 +332,14 @@ def rel_l2_vs_oracle(y, x):
     return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
 
 
-def form_errors(paco, forms, lg1: int = 12, lg2: int = 12, b: int = 4):
-    """Relative L2 error of each form against the FP64 oracle on one
-    2^(lg1+lg2)-point transform of the headline recipe (U[-1,1), seed 0)."""
-    import numpy as np
-    import torch
-
-    from paco_inputs import uniform
-    N1, N2 = 1 << lg1, 1 << lg2
-    x = uniform(N1 * N2, 0, np.complex64)
-    xt = torch.from_numpy(x).cuda()
-    out = {}
-    for name, dt in forms:
-        pl = paco.Plan(N1, N2, b, 1, dt)
-        y = torch.empty_like(xt)
-        pl.execute(xt, y, -1)
-        torch.cuda.synchronize()
-        pl.check()
-        out[name] = rel_l2_vs_oracle(y.cpu().numpy(), x)
-        pl.close()
-    return out
-
-
-def tc_split(paco, x, y, N1, N2, b, p, K, warmup, stream, flop, world, max_over_ranks):
+def tc_split(paco, x, y, N1, N2, b, p, K, warmup, stream, flop, world, max_over_ranks, plain_plan=None):
     """The tensor-core sub-DFT forms on the headline transform: time per step
-    (two launches of the TC stage kernel) and error at 2^24 against the
-    oracle, next to the plain form's error."""
+    and, for each form and for the plain form, the relative L2 error of that
+    same timed transform (the same input buffer) against the FP64 oracle."""
+    import numpy as np
     res = {}
     KT = max(min(K, 50), 5)
+    outs = {}
     for name, dt in (("bf16x3", paco.C64_TC_BF16X3), ("fp16", paco.C64_TC_FP16)):
         pl = paco.Plan(N1, N2, b, 1, dt, p=p)
         tot, per = time_steps(lambda: pl.execute(x, y, -1, stream), KT, warmup, stream)
@@ -357,24 +347,40 @@ def tc_split(paco, x, y, N1, N2, b, p, K, warmup, stream, flop, world, max_over_
         ms = max_over_ranks(tot) / KT
         res[name] = {"ms_per_step": ms, "value": flop * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
                      "steps": KT, "kernel": "paco_stage_kernel, radix-16 passes as mma.sync contractions"}
+        torch_sync()
+        outs[name] = y.cpu().numpy()
         pl.close()
-    errs = form_errors(paco, [("plain", paco.C64), ("bf16x3", paco.C64_TC_BF16X3),
-                              ("fp16", paco.C64_TC_FP16)])
-    for k, v in errs.items():
-        res.setdefault(k, {})["rel_l2"] = v
-    res["error_measured_on"] = "one 2^24 transform (4096 x 4096, b=4), U[-1,1) seed 0, vs the FP64 oracle"
+    if plain_plan is not None:
+        plain_plan.execute(x, y, -1, stream)
+        torch_sync()
+        outs["plain"] = y.cpu().numpy()
+    import oracle
+    ref = oracle.fft(x.cpu().numpy().astype(np.complex128).reshape(1, -1), threads=0).reshape(-1)
+    nref = float(np.linalg.norm(ref))
+    for k, v in outs.items():
+        res.setdefault(k, {})["rel_l2"] = float(np.linalg.norm(v.astype(np.complex128) - ref) / nref)
+    res["error_measured_on"] = (f"the timed transform itself (N = {N1} x {N2}, b={b}, same input), "
+                                "vs the FP64 oracle's full FFT")
     return res
 
 
-def cpu_leg(args, rank, world, dtype="c64", lg=None):
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def cpu_leg(args, rank, world, dtype="c64", lg=None, threads=None):
+    """The oracle timed on the host: all the cores this process may use
+    (default), or `threads` of them."""
     if rank != 0 or world != 1 or args.no_cpu_baseline:
         return None
     lg = args.cpu_lg if lg is None else lg
+    nt = host_cores() if threads is None else threads
     try:
-        g, per, reps = oracle_sample(lg, args.cpu_seconds, dtype)
-        return {"value": g, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+        g, per, reps = oracle_sample(lg, args.cpu_seconds / 2, dtype, nt)
+        return {"value": g, "unit": "GFLOP/s", "cores": nt, "kind": "oracle",
                 "sample": f"{reps} x one 2^{lg}-point transform (same recipe), "
-                          f"FP64 recursive radix-2 oracle, 1 thread, {per:.2f} s each"}
+                          f"FP64 recursive radix-2 oracle, {nt} thread(s), {per:.2f} s each"}
     except Exception as e:  # report, do not hide
         return {"value": None, "unit": "GFLOP/s", "cores": 0, "kind": "oracle", "sample": f"failed: {e}"}
 
@@ -842,10 +848,12 @@ def main():
 
     tc = None
     if args.dtype == "c64" and not args.no_tc:
-        tc = tc_split(paco, x, out, N1, N2, args.b, args.p, K, args.warmup, stream, flop, world, max_over_ranks)
+        tc = tc_split(paco, x, out, N1, N2, args.b, args.p, K, args.warmup, stream, flop, world, max_over_ranks,
+                      plain_plan=plan)
         tc["plain"].update({"ms_per_step": ms_step, "value": value, "unit": "GFLOP/s"})
 
     cpu = cpu_leg(args, rank, world, args.dtype)
+    cpu1 = cpu_leg(args, rank, world, args.dtype, threads=1)
     context = cufft_context(x, N, 1, flop)
 
     if rank == 0:
@@ -861,8 +869,8 @@ def main():
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic,
                          "algorithmic_bytes_per_launch": bytes_per_launch},
-            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": 2 * K, "clocks": clocks,
-            "tc_split": tc, "context": context,
+            "e2e": e2e, "cpu_baseline": cpu, "cpu_baseline_1core": cpu1, "gpu_launches": 2 * K,
+            "clocks": clocks, "tc_split": tc, "context": context,
         }
         print(json.dumps(line), flush=True)
     ranks.close()

@@ -66,27 +66,28 @@ def test_finite_differences_complex64():
 
 
 def test_analytic_adjoint_full_size():
-    """256 x N = 2^20 (config E): the GPU gradient against 2 F^H (w * F x)
-    from the oracle, on sampled entries of every 32nd transform."""
+    """256 x N = 2^20 (the differentiation workload): the GPU gradient of
+    L = sum(w |F x|^2) against 2 F^H (w * F x) computed by the oracle, for
+    every transform, element by element: relative L2 error per transform
+    <= 5e-7 * log2 N."""
     N1 = N2 = 1024
     N = N1 * N2
     batch = 256
-    x = torch.from_numpy(gaussian(batch * N, 0, np.complex64)).reshape(batch, N).cuda()
-    wt = torch.from_numpy(weights(batch * N, 1)).reshape(batch, N).cuda()
+    xh = gaussian(batch * N, 0, np.complex64).reshape(batch, N)
+    wh = weights(batch * N, 1).reshape(batch, N)
+    x = torch.from_numpy(xh).cuda()
+    wt = torch.from_numpy(wh).cuda()
     x.requires_grad_(True)
     y = paco.PacoFFT.apply(x, N1, N2, 4, 4)
     (wt * y.abs() ** 2).sum().backward()
-    g = x.grad
-    rng = np.random.default_rng(2)
-    tol = 5e-7 * math.log2(N) * 2
-    for t in range(0, batch, 32):
-        xt = x[t].detach().cpu().numpy().astype(np.complex128)
-        wtn = wt[t].cpu().numpy().astype(np.float64)
-        yt = oracle.fft(xt, -1)
-        js = rng.integers(0, N, 8)
-        want = 2 * oracle.dft_at(wtn * yt, js, +1)
-        got = g[t].cpu().numpy()[js].astype(np.complex128)
-        rms = np.sqrt(np.mean(np.abs(2 * oracle.fft(wtn * yt, +1)) ** 2))
-        assert np.max(np.abs(got - want)) / rms <= tol
-    del x, wt, y, g
+    g = x.grad.cpu().numpy()
+    del x, wt, y
     torch.cuda.empty_cache()
+    yo = oracle.fft(xh.astype(np.complex128), -1, threads=0)
+    yo *= wh.astype(np.float64)
+    want = oracle.fft(yo, +1, threads=0)
+    want *= 2.0
+    del yo
+    errs = np.linalg.norm(g.astype(np.complex128) - want, axis=1) / np.linalg.norm(want, axis=1)
+    tol = 5e-7 * math.log2(N)
+    assert float(errs.max()) <= tol, f"max rel_l2 {errs.max():.3e} over {batch} gradients"

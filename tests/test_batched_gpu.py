@@ -137,7 +137,9 @@ def test_empty_and_errors():
 def test_full_size_uneven_batch():
     """The uneven benchmark workload: 4096 lengths (exponents uniform over
     8..20, reduced to a 2^28 total) plus 2^14 transforms of 2^12, N(0,1).
-    Sampled transforms of every length against the oracle; Parseval for all."""
+    Every one of the 20 480 transforms, element by element, against the
+    oracle's FP64 FFT (grouped by length, the oracle's batch spread over the
+    host cores): relative L2 error <= 5e-7 * log2 N_i per transform."""
     e = uneven_lengths()
     lengths = np.concatenate([2 ** e, np.full(2 ** 14, 2 ** 12)]).astype(np.int64)
     total = int(lengths.sum())
@@ -149,30 +151,19 @@ def test_full_size_uneven_batch():
     plan.execute(x, out, -1)
     torch.cuda.synchronize()
     plan.check()
-    # Parseval per transform: sum |y|^2 = N sum |x|^2
-    off = torch.from_numpy(offsets(lengths)).cuda()
-    seg = torch.repeat_interleave(torch.arange(len(lengths), device="cuda"),
-                                  torch.from_numpy(lengths).cuda())
-    ex = torch.zeros(len(lengths), dtype=torch.float64, device="cuda")
-    ey = torch.zeros_like(ex)
-    ex.index_add_(0, seg, (x.abs() ** 2).double())
-    ey.index_add_(0, seg, (out.abs() ** 2).double())
-    n = torch.from_numpy(lengths).cuda().double()
-    rel = ((ey - n * ex).abs() / (n * ex)).max().item()
-    assert rel <= 1e-5, rel
-    # sampled parity: a few transforms of every length
-    rng = np.random.default_rng(7)
-    pick = []
+    xh = x.cpu().numpy()
+    yh = out.cpu().numpy()
+    del x, xr, out
+    torch.cuda.empty_cache()
+    offs = offsets(lengths)
+    worst = {}
     for v in np.unique(lengths):
         ids = np.flatnonzero(lengths == v)
-        pick += list(rng.choice(ids, size=min(3, len(ids)), replace=False))
-    offs = offsets(lengths)
-    xs, ys = {}, {}
-    for i in pick:
-        a, b = int(offs[i]), int(offs[i + 1])
-        xs[i] = x[a:b].cpu().numpy()
-        ys[i] = out[a:b].cpu().numpy()
-    for i in pick:
-        ref = oracle.fft(xs[i].astype(np.complex128))
-        err = np.linalg.norm(ys[i] - ref) / np.linalg.norm(ref)
-        assert err <= 5e-7 * math.log2(lengths[i]), (i, lengths[i], err)
+        n = int(v)
+        xs = np.stack([xh[offs[i]:offs[i] + n] for i in ids]).astype(np.complex128)
+        ys = np.stack([yh[offs[i]:offs[i] + n] for i in ids]).astype(np.complex128)
+        ref = oracle.fft(xs, -1, threads=0)
+        errs = np.linalg.norm(ys - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        worst[n] = float(errs.max())
+        assert worst[n] <= 5e-7 * math.log2(n), (n, worst[n], int(ids[int(np.argmax(errs))]))
+    assert sum(int(np.count_nonzero(lengths == n)) for n in worst) == len(lengths)
