@@ -19,7 +19,7 @@
 #include "../../include/paco.h"
 #include "paco_plan.h"
 #include "paco_common.cuh"
-#include "paco_panel.cuh"
+#include "paco_panel_host.h"
 #include "paco_stage.cuh"
 
 namespace paco {
@@ -27,8 +27,6 @@ const void *stage_kernel_fn_f32(int lgL, int minb);
 const void *stage_kernel_fn_f64(int lgL, int minb);
 const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
-const void *panel_kernel_fn();
-int panel_smem_bytes();
 } // namespace paco
 
 using namespace paco;
@@ -145,9 +143,10 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         req_w == 0 && req_k == 0) {
         sc->panel = 1;
         sc->P = kPanelWidth;
-        sc->fn = panel_kernel_fn();
+        sc->fn = panel_kernel_fn(mode, pl->b);
+        if (!sc->fn) return fail(PACO_ERR_UNSUPPORTED, "panel stage: radix %d", pl->b);
         sc->smem = panel_smem_bytes();
-        sc->threads = panel::NT + 32;                        // 16 consumer warps + 1 producer
+        sc->threads = panel::NT;                             // 16 consumer warps + producer + storer
         PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sc->smem));
         return PACO_OK;
     }
@@ -356,127 +355,32 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
 // ---------------------------------------------------------------------------
 // execution
 // ---------------------------------------------------------------------------
-// cuTensorMapEncodeTiled through the runtime's driver entry point.
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    }
-    return fn;
-}
-
-// 8-byte elements, no swizzle, box copied as is.
-static bool encode_map(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims,
-                       const cuuint64_t *strides, const cuuint32_t *box, bool promote)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_encoder();
-    if (!enc) return false;
-    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<void *>(base), dims,
-                     strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-// Tensor maps for one panel-stage launch.  Stage 2 reads, for a fixed j_lo,
-// the 128 rows pi_m2(j_lo + 128 j_hi) of W: pi is a bit permutation, so these
-// rows are the rows whose bits outside `vmask` equal those of pi(j_lo); the
-// row index splits into runs of consecutive spanned / fixed bits, one tensor
-// dimension each (box = the run's size, or 1), the top run carrying the batch.
-static bool panel_maps(const paco_plan *pl, const StageCfg &sc, int mode, const void *in, PanelArgs *a)
-{
-    const int E = 8;
-    if (mode == 1) {
-        const cuuint64_t dims[4] = {(cuuint64_t)pl->N2, 128, 128, (cuuint64_t)pl->batch};
-        const cuuint64_t str[3] = {(cuuint64_t)pl->N2 * E, (cuuint64_t)pl->N2 * 128 * E, (cuuint64_t)pl->N * E};
-        const cuuint32_t box[4] = {16, 4, 128, 1};
-        if (!encode_map(&a->map_in, in, 4, dims, str, box, true)) return false;
-        // scratch [c][j_lo >> 3][k_lo][j_lo & 7] as (j_lo & 7, k_lo, j_lo >> 3, c)
-        const cuuint64_t sdims[4] = {8, 128, 16, (cuuint64_t)sc.P * panel::NBUF};
-        const cuuint64_t sstr[3] = {8 * E, 128 * 8 * E, 16 * 128 * 8 * E};
-        const cuuint32_t sbox[4] = {8, 64, 16, 1};
-        return encode_map(&a->map_scr, pl->scratch, 4, sdims, sstr, sbox, false);
-    }
-    const int bits = pl->m2 * pl->t;                 // log2 N2 = 14
-    unsigned vmask = 0;
-    for (int jh = 0; jh < 128; ++jh) vmask |= (unsigned)paco_digit_reverse((int64_t)jh << 7, pl->b, pl->m2);
-    int starts[8], fixed[8], nr = 0;
-    for (int bit = 0; bit < bits; ++bit) {
-        const int f = !((vmask >> bit) & 1u);
-        if (nr == 0 || fixed[nr - 1] != f) {
-            if (nr == 8) return false;
-            starts[nr] = bit;
-            fixed[nr] = f;
-            ++nr;
-        }
-    }
-    if (nr > 4 || !fixed[nr - 1]) return false;      // rank <= 5, batch folds into a fixed top run
-    cuuint64_t dims[5], str[4];
-    cuuint32_t box[5];
-    dims[0] = (cuuint64_t)pl->N1;
-    box[0] = 64;
-    for (int k = 0; k < nr; ++k) {
-        const int en = (k + 1 < nr) ? starts[k + 1] : bits;
-        const cuuint64_t size = 1ull << (en - starts[k]);
-        dims[k + 1] = (k + 1 == nr) ? size * (cuuint64_t)pl->batch : size;
-        str[k] = ((cuuint64_t)pl->N1 * E) << starts[k];
-        box[k + 1] = fixed[k] ? 1u : (cuuint32_t)size;
-        a->map_run_start[k] = starts[k];
-        a->map_run_fixed[k] = fixed[k];
-    }
-    a->map_rank = nr + 1;
-    a->vmask = vmask;
-    if (!encode_map(&a->map_in, in, nr + 1, dims, str, box, true)) return false;
-    const cuuint64_t sdims[2] = {(cuuint64_t)sc.P, (cuuint64_t)panel::NBUF * 128 * 128};
-    const cuuint64_t sstr[1] = {(cuuint64_t)sc.P * E};
-    const cuuint32_t sbox[2] = {64, 128};
-    return encode_map(&a->map_scr, pl->scratch, 2, sdims, sstr, sbox, false);
-}
-
 static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int mode,
                                   const void *in, void *out, int dir, cudaStream_t stream)
 {
+    PanelLaunch l;
+    memset(&l, 0, sizeof(l));
+    l.mode = mode;
+    l.b = pl->b;
+    l.C = (mode == 1) ? pl->N2 : pl->N1;
+    l.batch = pl->batch;
+    l.N = pl->N;
+    l.P = sc.P;
+    l.in = in;
+    l.out = out;
+    l.scratch = pl->scratch;
+    l.ctr = pl->ctr;
+    l.status = pl->d_status;
+    l.twL = (mode == 1) ? pl->twL1 : pl->twL2;
+    l.twN_lo = pl->twN_lo;
+    l.twN_hi = pl->twN_hi;
+    l.twN_lo_bits = pl->twN_lo_bits;
+    l.conj = (dir == 1);
+    l.spin_limit = pl->dbg_spin_limit;
+    l.dep_bias = pl->dbg_wait_bias;
     PanelArgs a;
-    memset(&a, 0, sizeof(a));
-    a.in = in;
-    a.out = out;
-    a.scratch = pl->scratch;
-    a.ctr = pl->ctr;
-    a.status = pl->d_status;
-    a.batch_stride = pl->N;
-    a.mode = mode;
-    a.P = sc.P;
-    a.rev_t = pl->t;
-    a.rev_bits = pl->m2 * pl->t;
-    a.conj = (dir == 1);
-    a.N_mask = (unsigned)(pl->N - 1);
-    a.twN_lo = pl->twN_lo;
-    a.twN_hi = pl->twN_hi;
-    a.twN_lo_bits = pl->twN_lo_bits;
-    a.spin_limit = pl->dbg_spin_limit ? pl->dbg_spin_limit : 1u << 22;
-    a.dep_bias = pl->dbg_wait_bias;
-    if (mode == 1) {
-        a.C = (int)pl->N2;
-        a.out_ld = (int)pl->N1;
-        a.twL = pl->twL1;
-    } else {
-        a.C = (int)pl->N1;
-        a.out_ld = (int)pl->N1;
-        a.twL = pl->twL2;
-    }
-    a.panels_per_batch = a.C / sc.P;
-    a.use_tensor = panel_maps(pl, sc, mode, in, &a) ? 1 : 0;
-    a.lgP = ilog2_exact(sc.P);
-    a.lgPpb = ilog2_exact(a.panels_per_batch);
-    a.npanels = (int)(pl->batch * a.panels_per_batch);
+    paco_status_t st = panel_prepare(l, &a);
+    if (st != PACO_OK) return st;
     const size_t words = (size_t)(2 * a.npanels + 1);
     PACO_CUDA_TRY(cudaMemsetAsync(pl->ctr, 0, words * sizeof(unsigned), stream));
     const long long total = 2LL * a.npanels * ((long long)panel::L / panel::TILE) * sc.P;

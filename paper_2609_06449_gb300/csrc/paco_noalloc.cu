@@ -27,13 +27,7 @@
 
 #include "../../include/paco.h"
 #include "paco_common.cuh"
-#include "paco_panel.cuh"
-
-namespace paco {
-const void *panel_kernel_fn();
-int panel_smem_bytes();
-void set_last_error(const char *msg);          // message for paco_last_error()
-} // namespace paco
+#include "paco_panel_host.h"
 
 using namespace paco;
 
@@ -88,12 +82,6 @@ std::mutex g_mutex;
 // to every dependency target of the bounded waits
 unsigned g_dbg_spin_limit = 0, g_dbg_wait_bias = 0;
 
-paco_status_t fail(paco_status_t st, const char *msg)
-{
-    set_last_error(msg);
-    return st;
-}
-
 // Set-up for the current device, once: symbol addresses, tables, attributes.
 paco_status_t setup(int dev, DeviceState **out)
 {
@@ -113,9 +101,12 @@ paco_status_t setup(int dev, DeviceState **out)
         s.lo = static_cast<float2 *>(p);
         if (cudaGetSymbolAddress(&p, g_twN_hi) != cudaSuccess) return fail(PACO_ERR_CUDA, "cudaGetSymbolAddress(twN_hi) failed");
         s.hi = static_cast<float2 *>(p);
-        if (cudaFuncSetAttribute(panel_kernel_fn(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 panel_smem_bytes()) != cudaSuccess)
-            return fail(PACO_ERR_CUDA, "cudaFuncSetAttribute failed");
+        for (int k = 0; k < 3; ++k) {
+            const void *fn = panel_kernel_fn(k == 0 ? 1 : 2, k == 2 ? 4 : 2);
+            if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, panel_smem_bytes()) !=
+                cudaSuccess)
+                return fail(PACO_ERR_CUDA, "cudaFuncSetAttribute failed");
+        }
         if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return fail(PACO_ERR_CUDA, "cudaDeviceGetAttribute failed");
         noalloc_tables_kernel<<<(unsigned)(kL / 256), 256>>>(s.twL, s.lo, s.hi);
@@ -126,113 +117,6 @@ paco_status_t setup(int dev, DeviceState **out)
     }
     *out = &s;
     return PACO_OK;
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!tried) {
-        tried = true;
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess && q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-    }
-    return fn;
-}
-
-bool encode(CUtensorMap *m, const void *base, int rank, const cuuint64_t *dims, const cuuint64_t *str,
-            const cuuint32_t *box, bool promote)
-{
-    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
-    if (!enc) return false;
-    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, (cuuint32_t)rank, const_cast<void *>(base), dims, str, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-               promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Arguments of one stage (mode 1: in -> out; mode 2: out in place).
-bool stage_args(const DeviceState &s, int mode, int b, int t, long long batch, const void *in, void *out,
-                int dir, PanelArgs *a)
-{
-    memset(a, 0, sizeof(*a));
-    const int E = 8;
-    a->in = in;
-    a->out = out;
-    a->scratch = s.scratch;
-    a->ctr = s.ctr;
-    a->status = s.status;
-    a->batch_stride = kN;
-    a->C = (int)kL;
-    a->out_ld = (int)kL;
-    a->P = kP;
-    a->lgP = 6;
-    a->panels_per_batch = (int)kPanelsPerBatch;
-    a->lgPpb = 8;
-    a->npanels = (int)(batch * kPanelsPerBatch);
-    a->mode = mode;
-    a->rev_t = t;
-    a->rev_bits = kLg;
-    a->twL = s.twL;
-    a->twN_lo = s.lo;
-    a->twN_hi = s.hi;
-    a->twN_lo_bits = kLg;
-    a->N_mask = (unsigned)(kN - 1);
-    a->conj = (dir == 1);
-    a->spin_limit = g_dbg_spin_limit ? g_dbg_spin_limit : 1u << 22;
-    a->dep_bias = g_dbg_wait_bias;
-    if (mode == 1) {
-        const cuuint64_t dims[4] = {(cuuint64_t)kL, 128, 128, (cuuint64_t)batch};
-        const cuuint64_t str[3] = {(cuuint64_t)kL * E, (cuuint64_t)kL * 128 * E, (cuuint64_t)kN * E};
-        const cuuint32_t box[4] = {16, 4, 128, 1};
-        const cuuint64_t sdims[4] = {8, 128, 16, (cuuint64_t)kP * panel::NBUF};
-        const cuuint64_t sstr[3] = {8 * E, 128 * 8 * E, 16 * 128 * 8 * E};
-        const cuuint32_t sbox[4] = {8, 64, 16, 1};
-        a->use_tensor = encode(&a->map_in, in, 4, dims, str, box, true) &&
-                        encode(&a->map_scr, s.scratch, 4, sdims, sstr, sbox, false);
-        return true;
-    }
-    // stage 2: rows pi(j_lo + 128 j_hi) of W as runs of spanned / fixed bits
-    const int m2 = kLg / t;
-    unsigned vmask = 0;
-    for (int jh = 0; jh < 128; ++jh) vmask |= (unsigned)paco_digit_reverse((int64_t)jh << 7, b, m2);
-    int starts[8], fixed[8], nr = 0;
-    for (int bit = 0; bit < kLg; ++bit) {
-        const int f = !((vmask >> bit) & 1u);
-        if (nr == 0 || fixed[nr - 1] != f) {
-            if (nr == 8) return false;
-            starts[nr] = bit;
-            fixed[nr] = f;
-            ++nr;
-        }
-    }
-    if (nr > 4 || !fixed[nr - 1]) return false;
-    cuuint64_t dims[5], str[4];
-    cuuint32_t box[5];
-    dims[0] = (cuuint64_t)kL;
-    box[0] = 64;
-    for (int k = 0; k < nr; ++k) {
-        const int en = (k + 1 < nr) ? starts[k + 1] : kLg;
-        const cuuint64_t size = 1ull << (en - starts[k]);
-        dims[k + 1] = (k + 1 == nr) ? size * (cuuint64_t)batch : size;
-        str[k] = ((cuuint64_t)kL * E) << starts[k];
-        box[k + 1] = fixed[k] ? 1u : (cuuint32_t)size;
-        a->map_run_start[k] = starts[k];
-        a->map_run_fixed[k] = fixed[k];
-    }
-    a->map_rank = nr + 1;
-    a->vmask = vmask;
-    const cuuint64_t sdims[2] = {(cuuint64_t)kP, (cuuint64_t)panel::NBUF * 128 * 128};
-    const cuuint64_t sstr[1] = {(cuuint64_t)kP * E};
-    const cuuint32_t sbox[2] = {64, 128};
-    a->use_tensor = encode(&a->map_in, out, nr + 1, dims, str, box, true) &&
-                    encode(&a->map_scr, s.scratch, 2, sdims, sstr, sbox, false);
-    return true;
 }
 
 } // namespace
@@ -257,19 +141,38 @@ extern "C" paco_status_t paco_execute_noalloc(const void *in, void *out, int b, 
     DeviceState *s = nullptr;
     paco_status_t st = setup(dev, &s);
     if (st != PACO_OK) return st;
-    const int t = (b == 2) ? 1 : 2;
     cudaStream_t cs = (cudaStream_t)stream;
-    const long long tiles = 2LL * batch * kPanelsPerBatch * (2 * kP);
+    const long long tiles = 2LL * batch * kPanelsPerBatch * ((long long)panel::L / panel::TILE) * kP;
     const unsigned grid = (unsigned)(s->num_sms < tiles ? s->num_sms : tiles);
     for (int mode = 1; mode <= 2; ++mode) {
+        PanelLaunch l;
+        memset(&l, 0, sizeof(l));
+        l.mode = mode;
+        l.b = b;
+        l.C = kL;
+        l.batch = batch;
+        l.N = kN;
+        l.P = kP;
+        l.in = (mode == 1) ? in : out;
+        l.out = out;
+        l.scratch = s->scratch;
+        l.ctr = s->ctr;
+        l.status = s->status;
+        l.twL = s->twL;
+        l.twN_lo = s->lo;
+        l.twN_hi = s->hi;
+        l.twN_lo_bits = kLg;
+        l.conj = (dir == 1);
+        l.spin_limit = g_dbg_spin_limit;
+        l.dep_bias = g_dbg_wait_bias;
         PanelArgs a;
-        if (!stage_args(*s, mode, b, t, batch, mode == 1 ? in : out, out, dir, &a))
-            return fail(PACO_ERR_UNSUPPORTED, "paco_execute_noalloc: tensor layout not supported");
+        paco_status_t st2 = panel_prepare(l, &a);
+        if (st2 != PACO_OK) return st2;
         const size_t words = (size_t)(2 * a.npanels + 1);
         if (cudaMemsetAsync(s->ctr, 0, words * sizeof(unsigned), cs) != cudaSuccess)
             return fail(PACO_ERR_CUDA, "paco_execute_noalloc: counter reset failed");
         void *params[] = {&a};
-        if (cudaLaunchKernel(panel_kernel_fn(), dim3(grid), dim3(panel::NT + 32), params,
+        if (cudaLaunchKernel(panel_kernel_fn(mode, b), dim3(grid), dim3(panel::NT), params,
                              (size_t)panel_smem_bytes(), cs) != cudaSuccess)
             return fail(PACO_ERR_CUDA, "paco_execute_noalloc: launch failed");
     }

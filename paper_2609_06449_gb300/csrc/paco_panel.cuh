@@ -7,10 +7,10 @@
 // w_L^{-k_lo j_lo} between them (Sect. 4.1, Fig. "cofft", Eq. twop).  The
 // analysis places the recursion frontier where a view fits in cache; on
 // GB300 the cache that holds a slab is the 129 MB L2.  So each stage runs the
-// two child groups of one panel (a group of columns) as two sub-passes:
+// two child groups of one panel (a group of P columns) as two sub-passes:
 //
-//   sub-pass A: 128-point DFTs over j_hi of tiles read from HBM; twiddle;
-//               written to an L2-resident panel buffer;
+//   sub-pass A: 128-point DFTs over j_hi of tiles read from HBM; twiddle
+//               w_L^{-k_lo j_lo}; written to an L2-resident panel buffer;
 //   sub-pass B: 128-point DFTs over j_lo of that buffer; stage epilogue
 //               (mode 1: top-level twiddle w_N^{-k1 c} and the digit-reversed
 //               row pi_m2(c) of W, Eq. (17); mode 2: natural-order output).
@@ -18,18 +18,30 @@
 // HBM is touched once per element per direction (the paper's two passes); the
 // intermediate lives in a ring of NBUF panel buffers sized to stay in L2 and
 // its lines are discarded from L2 once consumed, so they are never written
-// back.  The tiles run in the order A0 | A1 B0 | A2 B1 | ... | B(np-1): a B
-// tile needs all A tiles of its panel; an A tile needs the panel that last
-// used its buffer to be consumed.
+// back.  Tiles run in the order A0 | A1 B0 | A2 B1 | ... | B(np-1): a B tile
+// needs all A tiles of its panel; an A tile needs the panel that last used
+// its buffer to be consumed.
 //
-// One persistent CTA per SM: a producer warp takes tiles from a global queue
-// in order, resolves their dependencies (bounded waits that record
-// PACO_ERR_TIMEOUT), builds the tile's twiddle tables and fills a ring of
-// NSTAGE shared-memory stage buffers with one tiled tensor TMA per tile
-// (cp.async.bulk.tensor, completion on an mbarrier).  Sixteen consumer warps
-// compute: every tile is 8192 elements, 16 per thread; a 128-point DFT is
-// radix 16 in registers, an exchange through the stage buffer (which first
-// was the tile's landing zone), then radix 8.
+// One persistent CTA per SM, three roles and no CTA-wide barrier:
+//   * a producer warp claims tiles from a global queue in order (one claim
+//     ahead), resolves their dependencies (bounded waits that record
+//     PACO_ERR_TIMEOUT) and lands each tile in one of NSTAGE shared-memory
+//     stage buffers with two tiled tensor TMA loads (boxes of 16 sequences x
+//     128 points, 128-byte swizzle); a table warp builds the tile's twiddle
+//     tables while the loads fly;
+//   * sixteen consumer warps in two groups of eight take alternate tiles; each
+//     warp owns four whole sequences of its tile: radix 16 in registers, the
+//     radix-16 -> radix-8 exchange inside the warp's own part of the stage
+//     buffer (warp synchronisation only), radix 8, the output twiddle;
+//     results are written back in place (or, for stage-1 A tiles, stored to
+//     the panel buffer with 16-byte stores);
+//   * a storer warp writes each finished tile out with two TMA tensor stores
+//     (one store group in flight), returns stage buffers to the producer once
+//     the stores have read them, and publishes the panel counters in batches
+//     (a release per run of tiles of one counter, and before every wait, so
+//     no CTA holds back a count another CTA waits for while it is idle).
+// The 128-byte swizzle makes every shared-memory access of a warp (landing
+// reads, both sides of the exchange, the output staging) conflict-free.
 #pragma once
 
 #include <cuda.h>                 // CUtensorMap (type only)
@@ -39,54 +51,55 @@
 namespace paco {
 
 struct PanelArgs {
-    // Tensor maps (__grid_constant__ parameter, 64-byte aligned):
-    //   map_in:  stage 1: X as (c, j_lo, j_hi, batch), box (16, 4, 128, 1);
-    //            stage 2: the rows of W split into runs of the bits that
-    //            pi_m2(j_lo + 128 j_hi) spans over j_hi (box: the run) or
-    //            fixes by j_lo (box 1), plus the columns, box 64 wide.
-    //   map_scr: stage 1: the scratch ring as (j_lo & 7, k_lo, j_lo >> 3, c),
-    //            box (8, 64, 16, 1); stage 2: as (v, rows), box (64, 128).
-    CUtensorMap map_in;
-    CUtensorMap map_scr;
-    int map_rank;                  // rank of map_in (stage 2)
-    int map_run_start[4];          // stage 2: first row bit of each row dimension
-    int map_run_fixed[4];          // 1: the run is fixed by j_lo (box 1), 0: spanned
-    unsigned vmask;                // stage 2: row bits spanned by j_hi
-    const void *in;                // stage input (batch of N elements)
-    void *out;                     // stage output
+    // Tensor maps (__grid_constant__ parameter, 64-byte aligned), all with
+    // 8-byte elements, 128-byte swizzle and 16-element inner boxes:
+    //   map_ld:     A-tile loads.  Stage 1: X as (c, j_lo, j_hi + 128 batch),
+    //               box (16, 1, 128).  Stage 2: the rows pi_m2(j_lo + 128 j_hi)
+    //               of W split into runs of row bits (see panel_prepare).
+    //   map_ld_alt: stage 2 with b = 4: map_ld moved by 64 rows (row bit 6,
+    //               fixed by j_lo, selects the map).
+    //   map_scr_ld: B-tile loads from the panel ring, box (16, 128, 1).
+    //   map_scr_st: stage 2: A-tile stores into the panel ring, box (16, 1, 128).
+    //   map_out:    B-tile stores.  Stage 1: W as (k_lo, k_hi, u + N2 batch),
+    //               box (16, 128, 1); stage 2: Y as (v, k_lo, k_hi + 128 batch),
+    //               box (16, 1, 128).
+    CUtensorMap map_ld;
+    CUtensorMap map_ld_alt;
+    CUtensorMap map_scr_ld;
+    CUtensorMap map_scr_st;
+    CUtensorMap map_out;
     void *scratch;                 // NBUF panel buffers of L*P elements
     unsigned *ctr;                 // [0] tile queue, [1..np] A done, [np+1..2np] B done
     int *status;                   // device status word (PACO_ERR_TIMEOUT)
-    long long batch_stride;
-    int C;                         // columns of the stage input matrix
-    int out_ld;                    // row length of the output matrix
     int P;                         // panel width (columns), a power of two >= 64
-    int lgP;                       // log2 P
+    int lgP;
     int panels_per_batch;          // C / P (a power of two)
-    int lgPpb;                     // log2 panels_per_batch
+    int lgPpb;
     int npanels;                   // batch * C / P
-    int mode;                      // 1: stage 1 fused with the middle stage; 2: stage 2
+    int N2rows;                    // stage 1: rows of W per transform (N2)
     int rev_bits, rev_t;           // digit reversal pi_m2
     const void *twL;               // w_L^{-r}, r < L
-    const void *twN_lo, *twN_hi;
+    const void *twN_lo, *twN_hi;   // w_N^{-r} in two levels (stage 1)
     int twN_lo_bits;
     unsigned N_mask;
-    int conj;
-    unsigned spin_limit;
-    int use_tensor;                // 1: tiles arrive by tensor TMA, 0: by bulk copies
+    int conj;                      // 1: conjugate on load and store (dir = +1)
+    unsigned spin_limit;           // poll limit of the dependency waits
     unsigned dep_bias;             // added to every dependency target (0; tests of the bounded waits)
 };
 
 namespace panel {
 
 constexpr int A = 128, B = 128, L = A * B;
-constexpr int SP = 66;              // exchange row stride (elements): conflict-free passes
-constexpr int NT = 512;             // consumer threads per CTA
-constexpr int TILE = 8192;          // elements per tile
-constexpr int NBUF = 3;             // panel buffers in the L2 ring
-constexpr int NSTAGE = 3;           // shared-memory stage buffers
-constexpr int STAGE_ELEMS = A * SP; // 8448 (>= 8192 landing)
-constexpr unsigned TILE_BYTES = TILE * 8;
+constexpr int NCW = 16;                  // consumer warps
+constexpr int WPG = 8;                   // consumer warps per group (one tile)
+constexpr int NT = (NCW + 3) * 32;       // + producer, storer and table warps
+constexpr int TILE = 4096;               // elements per tile (32 sequences x 128)
+constexpr int NBOX = 2;                  // TMA boxes per tile
+constexpr int NBUF = 3;                  // panel buffers in the L2 ring
+constexpr int NSTAGE = 6;                // shared-memory stage buffers
+constexpr unsigned BOX_BYTES = 16384;    // 16 sequences x 128 points x 8 B
+constexpr unsigned TILE_BYTES = NBOX * BOX_BYTES;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // give up an mbarrier wait after 2 s
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
 {
@@ -109,15 +122,20 @@ __device__ __forceinline__ unsigned long long policy_evict_last()
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
     return p;
 }
-__device__ __forceinline__ void st_hint(float2 *p, float2 v, unsigned long long pol)
+__device__ __forceinline__ void st_v4_hint(void *p, float4 v, unsigned long long pol)
 {
-    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;"
-                 :: "l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
 }
 __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void red_relaxed_add(unsigned *p, unsigned v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 // drop a consumed 128-byte scratch line from L2 without writing it back
 __device__ __forceinline__ void discard_l2(const void *p)
 {
@@ -127,44 +145,6 @@ __device__ __forceinline__ void discard_l2(const void *p)
 __device__ __forceinline__ float2 f2mul(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// Twiddles of a thread computed in registers from a few table entries (a
-// shared-memory read costs more than the products here: the consumers are
-// bound by shared-memory traffic).  seq8: out[k] = b * s^k, k < 8, from b,
-// s and s^4; at most four roundings on top of the tables'.
-__device__ __forceinline__ void seq8(float2 *out, float2 b, float2 s1, float2 s4)
-{
-    const float2 s2 = f2mul(s1, s1), s3 = f2mul(s2, s1);
-    out[0] = b;
-    out[1] = f2mul(b, s1);
-    out[2] = f2mul(b, s2);
-    out[3] = f2mul(b, s3);
-    const float2 b4 = f2mul(b, s4);
-    out[4] = b4;
-    out[5] = f2mul(b4, s1);
-    out[6] = f2mul(b4, s2);
-    out[7] = f2mul(b4, s3);
-}
-
-// exchange slot of sequence (jl, c) in the stage-1 A tile: conflict-free both
-// when lanes run over c (pass 1) and over jl then c (pass 2)
-__device__ __forceinline__ int slot_s1a(int jl, int c) { return c * 4 + (jl ^ ((c >> 2) & 3)); }
-
-// Pass 2: groups g = 2 gp + h (h < 2): radix 8 over t of exchange rows g*8 + t;
-// the output k' of group g is DFT index k = g + 16 k', left in v[8 h + k'].
-__device__ __forceinline__ void pass2(cx<float> *v, const float2 *sm, int gp, int slot)
-{
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int g = 2 * gp + h;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            float2 a = sm[(g * 8 + t) * SP + slot];
-            v[8 * h + t] = make_cx<float>(a.x, a.y);
-        }
-        dft8(v + 8 * h);
-    }
 }
 
 // ---- mbarrier / TMA ------------------------------------------------------
@@ -185,49 +165,51 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ unsigned mbar_try_wait(unsigned long long *bar, unsigned parity)
+// non-blocking test of the completion of the phase of the given parity
+__device__ __forceinline__ unsigned mbar_test(unsigned long long *bar, unsigned parity)
 {
     unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                  " selp.u32 %0, 1, 0, p;\n}"
                  : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
     return ok;
 }
-// Bounded wait for an mbarrier phase; returns 0 when it gave up.
-__device__ __forceinline__ int mbar_wait(unsigned long long *bar, unsigned parity, unsigned limit)
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about 0.5 ms pass, instead of spinning on the issue slots.
+__device__ __forceinline__ unsigned mbar_try_wait(unsigned long long *bar, unsigned parity)
 {
-    unsigned it = 0;
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(500000u) : "memory");
+    return ok;
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for the completion of the mbarrier phase of the given parity;
+// returns 0 when it gave up after `limit_ns` nanoseconds.
+__device__ __forceinline__ int mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return 1;
+    const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (++it > limit) return 0;
+        if (global_ns() - t0 > limit_ns) return 0;
     return 1;
 }
-// global -> shared bulk copy; `bytes` and both addresses multiples of 16
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes,
+__device__ __forceinline__ void tma_ld_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
                                           unsigned long long *bar, unsigned long long pol)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-                 " [%0], [%1], %2, [%3], %4;"
-                 :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int c0, int c1,
-                                       unsigned long long *bar, unsigned long long pol)
-{
-    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
-                 " [%0], [%1, {%2, %3}], [%4], %5;"
-                 :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(smem_u32(bar)), "l"(pol)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
-                                       unsigned long long *bar, unsigned long long pol)
 {
     asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
                  " [%0], [%1, {%2, %3, %4}], [%5], %6;"
                  :: "r"(smem_u32(dst)), "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "l"(pol)
                  : "memory");
 }
-__device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                       unsigned long long *bar, unsigned long long pol)
+__device__ __forceinline__ void tma_ld_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          unsigned long long *bar, unsigned long long pol)
 {
     asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
                  " [%0], [%1, {%2, %3, %4, %5}], [%6], %7;"
@@ -235,8 +217,8 @@ __device__ __forceinline__ void tma_4d(void *dst, const CUtensorMap *map, int c0
                     "l"(pol)
                  : "memory");
 }
-__device__ __forceinline__ void tma_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                       int c4, unsigned long long *bar, unsigned long long pol)
+__device__ __forceinline__ void tma_ld_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          int c4, unsigned long long *bar, unsigned long long pol)
 {
     asm volatile("cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
                  " [%0], [%1, {%2, %3, %4, %5, %6}], [%7], %8;"
@@ -244,11 +226,48 @@ __device__ __forceinline__ void tma_5d(void *dst, const CUtensorMap *map, int c0
                     "r"(smem_u32(bar)), "l"(pol)
                  : "memory");
 }
+__device__ __forceinline__ void tma_st_3d(const CUtensorMap *map, int c0, int c1, int c2, const void *src,
+                                          unsigned long long pol)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group.L2::cache_hint"
+                 " [%0, {%1, %2, %3}], [%4], %5;"
+                 :: "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(src)), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
-__device__ __forceinline__ void named_barrier_consumers()
+
+__device__ __forceinline__ float2 lds2(unsigned addr)
 {
-    asm volatile("bar.sync 1, %0;" :: "n"(NT) : "memory");
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts2(unsigned addr, float2 v)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" :: "r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// Stage-2 A tiles (rows of W read through the digit reversal): the landing
+// row of logical j_hi = t8 + 8 s is lo(t8) + 8 hi(s), fixed by the order of
+// the row dimensions of map_ld (see panel_prepare).  b = 2: the row
+// dimensions are (pi bits 4-6, pi bits 0-3): lo = 3-bit reversal, hi = 4-bit
+// reversal.  b = 4: (pi bit 7, pi bits 4-5, pi bits 0-3): lo = identity,
+// hi swaps the two bit pairs of s.
+template <int B2>
+__host__ __device__ constexpr int land_lo(int t8)
+{
+    return B2 == 2 ? (((t8 & 1) << 2) | (t8 & 2) | ((t8 >> 2) & 1)) : t8;
+}
+template <int B2>
+__host__ __device__ constexpr int land_hi(int s)
+{
+    return B2 == 2 ? (((s & 1) << 3) | ((s & 2) << 1) | ((s >> 1) & 2) | ((s >> 3) & 1))
+         : B2 == 4 ? (((s & 3) << 2) | ((s >> 2) & 3))
+                   : s;
 }
 
 } // namespace panel
@@ -274,8 +293,8 @@ __device__ __forceinline__ Tile decode_tile(int g, int lgT, int np)
     return d;
 }
 
-// tiles per phase per panel: L * P / TILE = 2 P
-__device__ __forceinline__ int tiles_per_phase(const PanelArgs &a) { return 2 << a.lgP; }
+// tiles per phase per panel: L * P / TILE = 4 P; a panel's counters complete there
+__device__ __forceinline__ unsigned tiles_per_phase(const PanelArgs &a) { return 4u << a.lgP; }
 
 // the counter a tile waits on, or nullptr
 __device__ __forceinline__ const unsigned *tile_dep(const PanelArgs &a, const Tile &d)
@@ -284,10 +303,25 @@ __device__ __forceinline__ const unsigned *tile_dep(const PanelArgs &a, const Ti
     if (d.q >= panel::NBUF) return a.ctr + 1 + a.npanels + (d.q - panel::NBUF);
     return nullptr;
 }
-
-__device__ __forceinline__ float2 *panel_buf(const PanelArgs &a, int q)
+// the counter a tile's completion counts towards
+__device__ __forceinline__ unsigned *tile_ctr(const PanelArgs &a, const Tile &d)
 {
-    return reinterpret_cast<float2 *>(a.scratch) + ((size_t)(q % panel::NBUF) << (14 + a.lgP));
+    return a.ctr + 1 + (d.isB ? a.npanels : 0) + d.q;
+}
+
+// Tile coordinates inside its panel (32 sequences).  Consecutive tiles cover
+// neighbouring column blocks of the same rows, so the CTAs working at one
+// time read and write whole 1 KiB panel rows:
+//   A tiles:     j_lo = t >> (lgP - 5), 32 columns from c0 = 32 (t & (P/32 - 1))
+//   stage-1 B:   column cl = t >> 2, 32 k_lo from k0 = 32 (t & 3)
+//   stage-2 B:   k_lo = t >> (lgP - 5), 32 columns from v0 = 32 (t & (P/32 - 1))
+__device__ __forceinline__ int tile_hi(const PanelArgs &a, const Tile &d, int mode)
+{
+    return (mode == 1 && d.isB) ? (d.t >> 2) : (d.t >> (a.lgP - 5));
+}
+__device__ __forceinline__ int tile_lo32(const PanelArgs &a, const Tile &d, int mode)
+{
+    return (mode == 1 && d.isB) ? ((d.t & 3) << 5) : ((d.t & ((a.P >> 5) - 1)) << 5);
 }
 
 // Lane 0 of the calling warp acquires `dep` (bounded blocking wait).
@@ -298,7 +332,7 @@ __device__ __forceinline__ int acquire_dep(const PanelArgs &a, const unsigned *d
     int ok = 1;
     if ((threadIdx.x & 31) == 0) {
         unsigned it = 0;
-        while (panel::ld_acquire(dep) < (unsigned)tiles_per_phase(a) + a.dep_bias) {
+        while (panel::ld_acquire(dep) < tiles_per_phase(a) + a.dep_bias) {
             if (++it > a.spin_limit) {
                 atomicExch(a.status, 5 /* PACO_ERR_TIMEOUT */);
                 ok = -1;
@@ -314,122 +348,72 @@ __device__ __forceinline__ int acquire_dep(const PanelArgs &a, const unsigned *d
 
 // ---- producer -------------------------------------------------------------
 
-// The copies of tile d into stage buffer sbuf (warp-wide call).  Landing
-// layouts (elements of the 8192-element tile):
-//   stage-1 A: (j_hi, jl, c)        at (j_hi*4 + jl)*16 + c
-//   stage-1 B: (j_lo>>3, k, j_lo&7) at ((j_lo>>3)*64 + k)*8 + (j_lo&7)
-//   stage-2 A: (landing row of j_hi, v) at lrow(j_hi)*64 + v  (tensor form);
-//              (j_hi, v) at j_hi*64 + v (bulk form)
-//   stage-2 B: (j, v)               at j*64 + v
-__device__ __forceinline__ void issue_tile(const PanelArgs &a, const Tile &d, float2 *sbuf,
-                                           unsigned long long *bar)
+// The two TMA loads of tile d into stage buffer sbuf (lane 0 of the producer).
+template <int MODE, int B2>
+__device__ __forceinline__ void issue_loads(const PanelArgs &a, const Tile &d, unsigned char *sbuf,
+                                            unsigned long long *bar)
 {
     using namespace panel;
-    const int lane = threadIdx.x & 31;
-    if (lane == 0) mbar_expect_tx(bar, TILE_BYTES);
-    __syncwarp();
+    mbar_expect_tx(bar, TILE_BYTES);
     const int bidx = d.q >> a.lgPpb, pcol = d.q & (a.panels_per_batch - 1);
-    const long long boff = (long long)bidx * a.batch_stride;
     const int colbase = pcol << a.lgP;
-    const float2 *gin = reinterpret_cast<const float2 *>(a.in);
-    const float2 *buf = panel_buf(a, d.q);
+    const int slot = d.q % NBUF;
+    const int hi = tile_hi(a, d, MODE), lo = tile_lo32(a, d, MODE);
     const unsigned long long pol = policy_evict_first();
-    if (a.use_tensor) {
-        if (lane != 0) return;
-        if (a.mode == 1 && !d.isB) {
-            const int j0 = (d.t >> (a.lgP - 4)) * 4, c0 = (d.t & ((a.P >> 4) - 1)) * 16;
-            tma_4d(sbuf, &a.map_in, colbase + c0, j0, 0, bidx, bar, pol);
-        } else if (a.mode == 1) {
-            const int cl = d.t >> 1, k0 = (d.t & 1) * 64;
-            tma_4d(sbuf, &a.map_scr, 0, k0, 0, ((d.q % NBUF) << a.lgP) + cl, bar, pol);
-        } else if (!d.isB) {
-            const int jlo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
-            const unsigned uf = digit_reverse((unsigned)jlo, a.rev_bits, a.rev_t);   // row bits fixed by j_lo
-            int c[5];
-            c[0] = colbase + v0;
-            const int R = a.map_rank;
-            for (int k = 1; k < R; ++k) {
-                const int st = a.map_run_start[k - 1];
-                const int en = (k < R - 1) ? a.map_run_start[k] : a.rev_bits;
-                c[k] = a.map_run_fixed[k - 1] ? (int)((uf >> st) & ((1u << (en - st)) - 1u)) : 0;
+#pragma unroll
+    for (int x = 0; x < NBOX; ++x) {
+        void *bx = sbuf + x * BOX_BYTES;
+        if (!d.isB) {
+            if (MODE == 1) {
+                tma_ld_3d(bx, &a.map_ld, colbase + lo + 16 * x, hi, bidx * 128, bar, pol);
+            } else {
+                const unsigned u = digit_reverse((unsigned)hi, a.rev_bits, a.rev_t);   // pi(j_lo): fixed row bits
+                if (B2 == 2) {
+                    tma_ld_4d(bx, &a.map_ld, colbase + lo + 16 * x, 0, 0, (int)(u >> 7) + (bidx << 7), bar, pol);
+                } else {
+                    const CUtensorMap *m = ((u >> 6) & 1u) ? &a.map_ld_alt : &a.map_ld;
+                    tma_ld_5d(bx, m, colbase + lo + 16 * x, 0, 0, 0, (int)(u >> 8) + (bidx << 6), bar, pol);
+                }
             }
-            c[R - 1] += bidx << (a.rev_bits - a.map_run_start[R - 2]);         // batch on the top run
-            if (R == 3) tma_3d(sbuf, &a.map_in, c[0], c[1], c[2], bar, pol);
-            else if (R == 4) tma_4d(sbuf, &a.map_in, c[0], c[1], c[2], c[3], bar, pol);
-            else tma_5d(sbuf, &a.map_in, c[0], c[1], c[2], c[3], c[4], bar, pol);
+        } else if (MODE == 1) {
+            tma_ld_3d(bx, &a.map_scr_ld, lo + 16 * x, 0, slot * a.P + hi, bar, pol);
         } else {
-            const int klo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
-            tma_2d(sbuf, &a.map_scr, v0, ((d.q % NBUF) << 14) + klo * B, bar, pol);
-        }
-        return;
-    }
-    // bulk-copy form (no tensor maps): one copy per contiguous run
-    if (a.mode == 1 && !d.isB) {
-        const int j0 = (d.t >> (a.lgP - 4)) * 4, c0 = (d.t & ((a.P >> 4) - 1)) * 16;
-        const float2 *src0 = gin + boff + colbase + c0;
-        for (int m = 0; m < 16; ++m) {
-            const int idx = lane + 32 * m, jh = idx >> 2, jl = idx & 3;
-            bulk_load(sbuf + idx * 16, src0 + (long long)(jh * B + j0 + jl) * a.C, 128, bar, pol);
-        }
-    } else if (a.mode == 1) {
-        const int cl = d.t >> 1, k0 = (d.t & 1) * 64;
-        if (lane < 16)
-            bulk_load(sbuf + lane * 512, buf + (((size_t)cl * 16 + lane) * A + k0) * 8, 4096, bar, pol);
-    } else if (!d.isB) {
-        const int jlo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
-        const float2 *src0 = gin + boff + colbase + v0;
-        for (int m = 0; m < 4; ++m) {
-            const int jh = lane + 32 * m;
-            const unsigned row = digit_reverse((unsigned)(jlo + (jh << 7)), a.rev_bits, a.rev_t);
-            bulk_load(sbuf + jh * 64, src0 + (long long)row * a.C, 512, bar, pol);
-        }
-    } else {
-        const int klo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
-        for (int m = 0; m < 4; ++m) {
-            const int j = lane + 32 * m;
-            bulk_load(sbuf + j * 64, buf + ((size_t)klo * B + j) * a.P + v0, 512, bar, pol);
+            tma_ld_3d(bx, &a.map_scr_ld, lo + 16 * x, 0, slot * 128 + hi, bar, pol);
         }
     }
 }
 
-// Twiddle tables of tile d for its stage (warp-wide call by the producer):
-//   A tiles: TW[k_lo*4 + jl] = w_L^{-k_lo j_lo}   (stage 2: jl = 0 only)
-//   stage-1 B: E1[k] = w_N^{-(k0+k) c},  E2[k_hi] = w_N^{-128 k_hi c}
-__device__ __forceinline__ void build_tables(const PanelArgs &a, const Tile &d, float2 *TW,
-                                             float2 *E1, float2 *E2, const float2 *w128,
-                                             const float2 *tlo)
+// Twiddle tables of tile d (warp-wide call by the producer):
+//   A tiles:    TW[k] = w_L^{-k j_lo}, k < 128, from the block's tables
+//               tlo[r] = w_L^{-r} and w128[r] = w_L^{-128 r} (r < 128)
+//   stage-1 B:  E1[e] = w_N^{-(k0+e) c} (e < 32), E2[k_hi] = w_N^{-128 k_hi c}
+template <int MODE>
+__device__ __forceinline__ void build_tables(const PanelArgs &a, const Tile &d, float2 *TW, float2 *E1,
+                                             float2 *E2, const float2 *tlo, const float2 *w128)
 {
     using namespace panel;
     const int lane = threadIdx.x & 31;
     if (!d.isB) {
-        if (a.mode == 1) {
-            const int j0 = (d.t >> (a.lgP - 4)) * 4;
-            for (int e = lane; e < 512; e += 32) {
-                const int klo = e >> 2, jl = e & 3;
-                const unsigned rr = (unsigned)(klo * (j0 + jl));                 // < L
-                TW[e] = f2mul(tlo[rr & 127], w128[rr >> 7]);
-            }
-        } else {
-            const int jlo = d.t >> (a.lgP - 6);
-            for (int klo = lane; klo < A; klo += 32) {
-                const unsigned rr = (unsigned)(klo * jlo);
-                TW[klo * 4] = f2mul(tlo[rr & 127], w128[rr >> 7]);
-            }
+        const unsigned jlo = (unsigned)tile_hi(a, d, MODE);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const unsigned r = (unsigned)(lane + 32 * m) * jlo;                 // < L
+            TW[lane + 32 * m] = f2mul(tlo[r & 127u], w128[r >> 7]);
         }
-    } else if (a.mode == 1) {
+    } else if (MODE == 1) {
         const int pcol = d.q & (a.panels_per_batch - 1);
-        const unsigned cglob = (unsigned)((pcol << a.lgP) + (d.t >> 1));
-        const int k0 = (d.t & 1) * 64;
+        const unsigned cglob = (unsigned)((pcol << a.lgP) + tile_hi(a, d, MODE));
+        const int k0 = tile_lo32(a, d, MODE);
         const float2 *nlo = reinterpret_cast<const float2 *>(a.twN_lo);
         const float2 *nhi = reinterpret_cast<const float2 *>(a.twN_hi);
         const unsigned lomask = (1u << a.twN_lo_bits) - 1u;
-        constexpr int PER = (64 + B) / 32;                   // 6 entries per lane
+        constexpr int PER = (32 + B) / 32;                   // 5 entries per lane
         float2 lo[PER], hi[PER];
 #pragma unroll
         for (int m = 0; m < PER; ++m) {                      // all loads in flight first
             const int e = lane + 32 * m;
-            const unsigned r = (e < 64) ? (((unsigned)(k0 + e) * cglob) & a.N_mask)
-                                        : (((unsigned)A * (unsigned)(e - 64) * cglob) & a.N_mask);
+            const unsigned r = (e < 32) ? (((unsigned)(k0 + e) * cglob) & a.N_mask)
+                                        : (((unsigned)A * (unsigned)(e - 32) * cglob) & a.N_mask);
             lo[m] = __ldg(nlo + (r & lomask));
             hi[m] = __ldg(nhi + (r >> a.twN_lo_bits));
         }
@@ -437,310 +421,412 @@ __device__ __forceinline__ void build_tables(const PanelArgs &a, const Tile &d, 
         for (int m = 0; m < PER; ++m) {
             const int e = lane + 32 * m;
             const float2 w = f2mul(lo[m], hi[m]);
-            if (e < 64) E1[e] = w; else E2[e - 64] = w;
+            if (e < 32) E1[e] = w; else E2[e - 32] = w;
         }
     }
 }
 
-// ---- consumers ------------------------------------------------------------
+// ---- consumer ---------------------------------------------------------------
 
-// Pass-1 operands of tile d from its landing layout; lrow[j_hi] is the landing
-// row of logical j_hi for stage-2 A tiles that arrive by tensor TMA (the box
-// keeps the physical row order of W).
-__device__ __forceinline__ void read_landing(const PanelArgs &a, const Tile &d, cx<float> *v,
-                                             const float2 *sbuf, const unsigned char *lrow)
+__device__ __forceinline__ void cmul_into(cx<float> &v, float2 w)
 {
-    const int tid = threadIdx.x;
-    if (a.mode == 1 && !d.isB) {
-        const int cc = tid & 15, jl = (tid >> 4) & 3, t8 = tid >> 6;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const float2 x = sbuf[((t8 + 8 * r) * 4 + jl) * 16 + cc];
-            v[r] = make_cx<float>(x.x, x.y);
-        }
-    } else if (a.mode == 1) {
-        const int t8 = tid & 7, k = tid >> 3;                 // lanes over (t8, k): consecutive words
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const float2 x = sbuf[(r * 64 + k) * 8 + t8];
-            v[r] = make_cx<float>(x.x, x.y);
-        }
-    } else if (!d.isB && a.use_tensor) {
-        const int vv = tid & 63, t8 = tid >> 6;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const float2 x = sbuf[lrow[t8 + 8 * r] * 64 + vv];
-            v[r] = make_cx<float>(x.x, x.y);
-        }
-    } else {
-        const int vv = tid & 63, t8 = tid >> 6;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const float2 x = sbuf[(t8 + 8 * r) * 64 + vv];
-            v[r] = make_cx<float>(x.x, x.y);
-        }
-    }
+    const float2 p = panel::f2mul(make_float2(v.x, v.y), w);
+    v.x = p.x;
+    v.y = p.y;
 }
 
-// Radix-16 pass of tile d in registers (conjugation of the stage input, DFT,
-// w_128^{-s t8} twiddles from w16[s*8 + t8]); returns the thread's t8 and its
-// exchange slot.
-__device__ __forceinline__ void pass1_regs(const PanelArgs &a, const Tile &d, cx<float> *v,
-                                           const float2 *w16, int &t8, int &slot)
+// One consumer warp's part of tile d in stage buffer sb (shared address):
+// warp wl (0..7 within its group) owns columns 4 (wl & 3) .. 4 (wl & 3) + 3
+// of box wl >> 2.  Lane l has q = l & 7 (t8 in pass 1, gp in pass 2) and
+// column c = 4 (wl & 3) + (l >> 3), so each half-warp (the unit an 8-byte
+// shared access is served in) holds all eight values of q for two columns
+// sharing a 16-byte chunk.
+// Shared address of (row r, column c) of a box: r*128 + ((c>>1) ^ (r&7))*16
+// + (c&1)*8 (the TMA 128-byte swizzle).
+// Pass 2 gives lane gp the sequence outputs k = k16 + 16 k8 for two k16:
+//   paired (stage-1 A, stored from registers as 16-byte pairs): k16 = 2gp + h;
+//   staged (all other tiles, written back as the store image): k16 = gp + 8h,
+//   so that the image rows k of the eight gp differ in k & 7.
+template <int MODE, int B2>
+__device__ __forceinline__ void consume_tile(const PanelArgs &a, const Tile &d, unsigned sb,
+                                             const float2 *TW, const float2 *E1, const float2 *E2,
+                                             const float2 *w16)
 {
     using namespace panel;
-    const int tid = threadIdx.x;
-    if (a.mode == 1 && !d.isB) {
-        const int cc = tid & 15, jl = (tid >> 4) & 3;
-        t8 = tid >> 6;
-        slot = slot_s1a(jl, cc);
-    } else if (a.mode == 1) {
-        t8 = tid & 7;
-        slot = tid >> 3;
-    } else {
-        t8 = tid >> 6;
-        slot = tid & 63;
+    const int wl = (threadIdx.x >> 5) & (WPG - 1), lane = threadIdx.x & 31;
+    const int q = lane & 7;
+    const int col = 4 * (wl & 3) + (lane >> 3);              // column in the box
+    const int cc = col >> 1, half = col & 1;
+    const unsigned box = sb + (unsigned)(wl >> 2) * BOX_BYTES + (unsigned)half * 8u;
+    const bool paired = (MODE == 1 && !d.isB);
+
+    cx<float> v[16];
+    // ---- landing -> registers: v[s] = logical point t8 + 8 s, t8 = q
+    {
+        const int lo = (MODE == 2 && !d.isB) ? land_lo<B2>(q) : q;
+        const unsigned base = box + (unsigned)(lo << 7) + (unsigned)((cc ^ lo) << 4);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const int hs = (MODE == 2 && !d.isB) ? land_hi<B2>(s) : s;
+            const float2 x = lds2(base + (unsigned)hs * 1024u);
+            v[s] = make_cx<float>(x.x, x.y);
+        }
     }
     if (!d.isB && a.conj) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r].y = -v[r].y;
+        for (int s = 0; s < 16; ++s) v[s].y = -v[s].y;
     }
     dft16(v);
-    // w_128^{-s t8} = z^s, z = w_128^{-t8}: z^(4a + c) = z4^a * z^c from the
-    // table entries z, z^4, z^8 (s = 1, 4, 8 of w16[s * 8 + t8])
-    const float2 z1 = w16[8 + t8], z4 = w16[32 + t8], z8 = w16[64 + t8];
-    const float2 z2 = f2mul(z1, z1), z3 = f2mul(z2, z1), z12 = f2mul(z8, z4);
-    const float2 zl[4] = {make_float2(1.f, 0.f), z1, z2, z3};
-    const float2 zh[4] = {make_float2(1.f, 0.f), z4, z8, z12};
 #pragma unroll
-    for (int s = 1; s < 16; ++s) {
-        float2 w;
-        if ((s & 3) == 0) w = zh[s >> 2];
-        else if ((s >> 2) == 0) w = zl[s & 3];
-        else w = f2mul(zh[s >> 2], zl[s & 3]);
-        const float2 p = f2mul(make_float2(v[s].x, v[s].y), w);
-        v[s].x = p.x; v[s].y = p.y;
+    for (int s = 1; s < 16; ++s) cmul_into(v[s], w16[s * 8 + q]);     // w_128^{-k16 t8}
+    // ---- exchange inside the warp's columns: X1[t8][k16] at row
+    // R = 8 k16 + (t8 ^ m(k16)), m = k16 >> 1 (paired) or k16 & 7 (staged);
+    // its row & 7 is a bijection of t8 (the writes) and of gp (the reads), so
+    // every access is conflict-free.
+    const unsigned e0 = box + (unsigned)(q << 7) + (unsigned)((cc ^ q) << 4);
+    __syncwarp();                                             // landing reads of the other lanes done
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        const unsigned m = paired ? (unsigned)(k >> 1) : (unsigned)(k & 7);
+        sts2((e0 ^ (m * 0x90u)) + (unsigned)k * 1024u, make_float2(v[k].x, v[k].y));
     }
-}
-
-// Radix-8 pass from the exchange layout and the stores of tile d.
-__device__ __forceinline__ void pass2_store(const PanelArgs &a, const Tile &d, cx<float> *v,
-                                            const float2 *sm, const float2 *TW, const float2 *E1,
-                                            const float2 *E2)
-{
-    using namespace panel;
-    const int tid = threadIdx.x;
-    const int bidx = d.q >> a.lgPpb, pcol = d.q & (a.panels_per_batch - 1);
-    const long long boff = (long long)bidx * a.batch_stride;
-    const int colbase = pcol << a.lgP;
-    float2 *buf = panel_buf(a, d.q);
-    float2 *gout = reinterpret_cast<float2 *>(a.out);
-    if (a.mode == 1 && !d.isB) {
-        // scratch layout [c][j_lo >> 3][k_lo][j_lo & 7]
-        const int j0 = (d.t >> (a.lgP - 4)) * 4, c0 = (d.t & ((a.P >> 4) - 1)) * 16;
-        const int jl = tid & 3, cc = (tid >> 2) & 15, gp = tid >> 6;
-        pass2(v, sm, gp, slot_s1a(jl, cc));
-        const int jlo = j0 + jl;
-        float2 *dst = buf + ((size_t)(c0 + cc) * 16 + (jlo >> 3)) * (A * 8) + (jlo & 7);
-        const unsigned long long pol = policy_evict_last();
-        // TW[klo][jl] = w_L^{-klo jlo}, klo = 2 gp + h + 16 k: b_h * s^k
-        const float2 s1 = TW[16 * 4 + jl], s4 = TW[64 * 4 + jl];
+    __syncwarp();
+    {
+        // paired: row 8 (2gp + h) + (t ^ gp); staged: row 8 (gp + 8h) + (t ^ gp)
+        const unsigned rb = e0 + (paired ? (unsigned)q * 2048u : (unsigned)q * 1024u);
+        const unsigned hs = paired ? 1024u : 8192u;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            float2 tw[8];
-            seq8(tw, TW[(2 * gp + h) * 4 + jl], s1, s4);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int klo = 2 * gp + h + 16 * k;
-                st_hint(dst + klo * 8, f2mul(make_float2(v[8 * h + k].x, v[8 * h + k].y), tw[k]), pol);
+            for (int t = 0; t < 8; ++t) {
+                const float2 x = lds2((rb ^ (unsigned)(t * 0x90)) + (unsigned)h * hs);
+                v[8 * h + t] = make_cx<float>(x.x, x.y);
             }
+            dft8(v + 8 * h);
         }
-    } else if (a.mode == 1) {
-        const int cl = d.t >> 1, k0 = (d.t & 1) * 64;
-        const unsigned cglob = (unsigned)(colbase + cl);
-        const int k = tid & 63, gp = tid >> 6;
-        pass2(v, sm, gp, k);
-        const unsigned urow = digit_reverse(cglob, a.rev_bits, a.rev_t);
-        float2 *dst = gout + boff + (long long)urow * a.out_ld + k0 + k;
-        const float2 e1 = E1[k];
-        const unsigned long long pol = policy_evict_first();
-        // E2[khi] = w_N^{-128 khi c}, khi = 2 gp + h + 16 kk: (e1 E2[2 gp + h]) * s^kk
-        const float2 s1 = E2[16], s4 = E2[64];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float2 tw[8];
-            seq8(tw, f2mul(e1, E2[2 * gp + h]), s1, s4);
-#pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int khi = 2 * gp + h + 16 * kk;
-                float2 y = f2mul(make_float2(v[8 * h + kk].x, v[8 * h + kk].y), tw[kk]);
-                if (a.conj) y.y = -y.y;
-                st_hint(dst + A * khi, y, pol);
-            }
-        }
-    } else if (!d.isB) {
-        // scratch layout [k_lo][j_lo][v]
-        const int jlo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
-        const int vv = tid & 63, gp = tid >> 6;
-        pass2(v, sm, gp, vv);
-        float2 *dst = buf + (size_t)jlo * a.P + v0 + vv;
-        const unsigned long long pol = policy_evict_last();
-        // TW[klo] = w_L^{-klo jlo}, klo = 2 gp + h + 16 k: b_h * s^k
-        const float2 s1 = TW[16 * 4], s4 = TW[64 * 4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float2 tw[8];
-            seq8(tw, TW[(2 * gp + h) * 4], s1, s4);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int klo = 2 * gp + h + 16 * k;
-                st_hint(dst + (size_t)klo * B * a.P, f2mul(make_float2(v[8 * h + k].x, v[8 * h + k].y), tw[k]), pol);
-            }
-        }
-    } else {
-        const int klo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
-        const int vv = tid & 63, gp = tid >> 6;
-        pass2(v, sm, gp, vv);
-        float2 *dst = gout + boff + colbase + v0 + vv;
-        const unsigned long long pol = policy_evict_first();
+    }
+    // v[8 h + k8] = output k = k16(h) + 16 k8 of the lane's sequence
+    const int kb0 = paired ? 2 * q : q, kbs = paired ? 1 : 8;   // k16(h) = kb0 + kbs h
+    if (!d.isB) {
+        // A tiles: w_L^{-k j_lo} = TW[k]
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const int khi = 2 * gp + h + 16 * kk;
-                float2 y = make_float2(v[8 * h + kk].x, a.conj ? -v[8 * h + kk].y : v[8 * h + kk].y);
-                st_hint(dst + (long long)(klo + A * khi) * a.out_ld, y, pol);
-            }
+            for (int k = 0; k < 8; ++k) cmul_into(v[8 * h + k], TW[kb0 + kbs * h + 16 * k]);
+    } else if (MODE == 1) {
+        // stage-1 B: w_N^{-(k_lo + 128 k_hi) c} = E1[column] E2[k_hi]
+        const float2 e1 = E1[16 * (wl >> 2) + col];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cmul_into(v[8 * h + k], f2mul(e1, E2[kb0 + kbs * h + 16 * k]));
     }
-}
-
-// Drop the consumed scratch lines of a B tile (one 128-byte line per thread).
-__device__ __forceinline__ void discard_consumed(const PanelArgs &a, const Tile &d)
-{
-    using namespace panel;
-    const int tid = threadIdx.x;
-    const float2 *buf = panel_buf(a, d.q);
-    if (a.mode == 1) {
-        const int cl = d.t >> 1, k0 = (d.t & 1) * 64;
-        discard_l2(buf + (((size_t)cl * 16 + (tid >> 5)) * A + k0) * 8 + 16 * (tid & 31));
+    if (d.isB && a.conj) {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) v[s].y = -v[s].y;
+    }
+    if (paired) {
+        // panel buffer [c][j_lo][k_lo]: 16-byte stores of (k, k + 1), k = 2q + 16 k8
+        const int jlo = tile_hi(a, d, MODE);
+        const int cl = tile_lo32(a, d, MODE) + 16 * (wl >> 2) + col;     // column in the panel
+        float2 *dst = reinterpret_cast<float2 *>(a.scratch) +
+                      ((((size_t)(d.q % NBUF) << a.lgP) + (size_t)cl) * 128 + (size_t)jlo) * 128 + 2 * q;
+        const unsigned long long pol = policy_evict_last();
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            st_v4_hint(dst + 16 * k, make_float4(v[k].x, v[k].y, v[8 + k].x, v[8 + k].y), pol);
     } else {
-        const int klo = d.t >> (a.lgP - 6), v0 = (d.t & ((a.P >> 6) - 1)) * 64;
-        discard_l2(buf + ((size_t)klo * B + (tid >> 2)) * a.P + v0 + 16 * (tid & 3));
+        // in place, row = output index k = q + 8h + 16 k8: the tile's store image
+        __syncwarp();                                         // exchange reads of the other lanes done
+        const unsigned ob = box + (unsigned)(q << 7) + (unsigned)((cc ^ q) << 4);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                sts2(ob + (unsigned)h * 1024u + (unsigned)k * 2048u, make_float2(v[8 * h + k].x, v[8 * h + k].y));
+        fence_async_shared();                                 // visible to the TMA stores
     }
 }
 
-// Warps 0..15 consume, warp 16 produces.  The producer takes tile indices in
-// queue order, resolves each tile's dependency (a bounded blocking wait is
-// safe there: a tile depends only on tiles dequeued before it), builds its
-// twiddle tables and fills stage buffer i % NSTAGE once the consumers have
-// released it; `full` carries data and tables, `empty` returns the buffer.
-__global__ void __launch_bounds__(panel::NT + 32, 1)
+// ---- storer ------------------------------------------------------------------
+
+// The storer's outstanding work: the stage whose store group is the newest
+// (its reads not yet confirmed) and the counter increments not yet published.
+struct StorerState {
+    int last_b;                    // stage of the newest store group, -1: none
+    unsigned *pa; unsigned na;     // pending completions of A tiles (panel counter, count)
+    int pa_async;                  // those A tiles were stored by TMA: publish after their writes
+    unsigned *pb; unsigned nb;     // pending completions of B tiles
+};
+
+__device__ __forceinline__ void storer_release_a(StorerState &st)
+{
+    if (!st.pa) return;
+    if (st.pa_async) {
+        panel::bulk_wait0();                                  // the stores are written
+        panel::fence_async_global();
+    }
+    panel::red_release_add(st.pa, st.na);
+    st.pa = nullptr;
+    st.na = 0;
+    st.pa_async = 0;
+}
+__device__ __forceinline__ void storer_release_b(StorerState &st)
+{
+    if (!st.pb) return;
+    panel::red_release_add(st.pb, st.nb);
+    st.pb = nullptr;
+    st.nb = 0;
+}
+// Everything outstanding: before the storer blocks, so that no count another
+// CTA (or this CTA's producer) waits for is held back by an idle storer.
+__device__ __forceinline__ void storer_flush(StorerState &st, unsigned long long *empty)
+{
+    if (st.last_b >= 0) {
+        panel::bulk_wait_read0();
+        panel::mbar_arrive(&empty[st.last_b]);
+        st.last_b = -1;
+    }
+    if (!st.pa && !st.pb) return;
+    if (st.pa && st.pa_async) {
+        panel::bulk_wait0();                                  // the stores are written
+        panel::fence_async_global();
+    }
+    panel::fence_acq_rel_gpu();                               // one fence publishes both counts
+    if (st.pa) panel::red_relaxed_add(st.pa, st.na);
+    if (st.pb) panel::red_relaxed_add(st.pb, st.nb);
+    st.pa = st.pb = nullptr;
+    st.na = st.nb = 0;
+    st.pa_async = 0;
+}
+
+// Warps 0..15 consume (groups 0 and 1 take even and odd tiles), warp 16
+// produces, warp 17 stores, warp 18 builds the twiddle tables.
+template <int MODE, int B2>
+__global__ void __launch_bounds__(panel::NT, 1)
     paco_panel_kernel(const __grid_constant__ PanelArgs args)
 {
     using namespace panel;
-    extern __shared__ __align__(1024) float2 stage[];     // NSTAGE x STAGE_ELEMS
-    __shared__ __align__(8) unsigned long long full[NSTAGE], empty[NSTAGE];
-    __shared__ float2 w128[A];                           // w_128^{-r} = w_L^{-128 r}
-    __shared__ float2 w16[128];                          // w_128^{-s t8} at [s*8 + t8]
-    __shared__ float2 tlo[128];                          // w_L^{-r}, r < 128
-    __shared__ float2 TWs[NSTAGE][512];                  // per-stage w_L table (A tiles)
-    __shared__ float2 E1s[NSTAGE][64], E2s[NSTAGE][B];   // per-stage w_N factors (stage-1 B)
-    __shared__ int s_info[NSTAGE];                       // tile index held by each stage
-    __shared__ unsigned char lrow[A];                    // stage 2 (tensor): landing row of j_hi
+    extern __shared__ __align__(1024) unsigned char stage_raw[];
+    __shared__ __align__(8) unsigned long long full[NSTAGE], done[NSTAGE], empty[NSTAGE], posted[NSTAGE];
+    __shared__ float2 w16[128];                           // w_128^{-s t8} at [s*8 + t8]
+    __shared__ float2 tlo[128], w128[128];                // w_L^{-r}, w_L^{-128 r}, r < 128
+    __shared__ float2 TWs[NSTAGE][128];                   // per-stage w_L table (A tiles)
+    __shared__ float2 E1s[NSTAGE][32], E2s[NSTAGE][B];    // per-stage w_N factors (stage-1 B)
+    __shared__ int s_info[NSTAGE];                        // tile index held by each stage
     __shared__ volatile int s_abort;
 
-    const int tid = threadIdx.x;
+    // the dynamic buffer starts 1024-aligned (the 128-byte swizzle needs it)
+    unsigned char *stage = stage_raw + ((1024u - (smem_u32(stage_raw) & 1023u)) & 1023u);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const float2 *twL = reinterpret_cast<const float2 *>(args.twL);
-    for (int r = tid; r < A; r += blockDim.x) {
-        w128[r] = __ldg(twL + r * B);
-        tlo[r] = __ldg(twL + r);
+    for (int r = tid; r < 128; r += blockDim.x) {
         w16[r] = __ldg(twL + ((r >> 3) * (r & 7)) * B);
-    }
-    if (tid < A && args.mode == 2) {
-        // landing row of j_hi: the spanned row bits of pi(j_hi * 128), packed
-        const unsigned u = digit_reverse((unsigned)tid << 7, args.rev_bits, args.rev_t);
-        unsigned r = 0;
-        int o = 0;
-        for (int bit = 0; bit < args.rev_bits; ++bit)
-            if ((args.vmask >> bit) & 1u) r |= ((u >> bit) & 1u) << o++;
-        lrow[tid] = (unsigned char)r;
+        tlo[r] = __ldg(twL + r);
+        w128[r] = __ldg(twL + r * B);
     }
     if (tid == 0) {
         for (int k = 0; k < NSTAGE; ++k) {
-            mbar_init(&full[k], 1);
+            mbar_init(&full[k], 2);                       // the load arrival (with bytes) + the tables
+            mbar_init(&done[k], WPG);
             mbar_init(&empty[k], 1);
+            mbar_init(&posted[k], 1);                     // the tile index is in s_info
+
         }
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const int lgT = args.lgP + 1;                        // T = 2 P tiles per phase
+    const int lgT = args.lgP + 2;                        // T = 4 P tiles per phase
     const int total = (2 * args.npanels) << lgT;
     __syncthreads();
 
-    if (tid >= NT) {
-        // ---------------- producer warp ----------------
-        const int lane = tid & 31;
-        unsigned eparity = 0;
-        for (int i = 0;; ++i) {
+    if (warp == NCW) {
+        // ---------------- producer ----------------
+        const unsigned *depA = nullptr, *depB = nullptr;  // the counters last found complete
+        int gnext = 0;
+        if (lane == 0) gnext = (int)atomicAdd(args.ctr, 1u);
+        int i = 0, ends = 0;
+        for (;; ++i) {
             const int b = i % NSTAGE;
-            if (i >= NSTAGE) {
-                int ok = 1;
-                if (lane == 0) ok = mbar_wait(&empty[b], (eparity >> b) & 1u, 1u << 22);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                eparity ^= 1u << b;
-                if (!ok && lane == 0) s_abort = 1;
+            if (i >= NSTAGE && lane == 0 &&
+                !mbar_wait(&empty[b], (unsigned)((i / NSTAGE - 1) & 1), WAIT_NS)) {
+                s_abort = 1;
+                atomicExch(args.status, 5);
+                // the stage was not returned: let its load land before reusing it
+                mbar_wait(&full[b], (unsigned)(((i - NSTAGE) / NSTAGE) & 1), WAIT_NS);
             }
+            __syncwarp();
             int g = 0;
             if (lane == 0) {
-                g = (int)atomicAdd(args.ctr, 1u);
-                if (s_abort) g = total;                      // stop: hand the consumers a terminator
+                g = s_abort ? total : gnext;
+                if (g < total && !ends) gnext = (int)atomicAdd(args.ctr, 1u);   // claim one ahead
             }
             g = __shfl_sync(0xffffffffu, g, 0);
+            if (ends) g = total;
             const Tile d = decode_tile(g, lgT, args.npanels);
-            if (g < total && acquire_dep(args, tile_dep(args, d)) < 0) {
-                if (lane == 0) s_abort = 1;
-                g = total;
+            bool fresh = false;                               // a dependency newly acquired
+            if (g < total) {
+                const unsigned *dep = tile_dep(args, d);
+                const unsigned *&cache = d.isB ? depB : depA;
+                if (dep && dep != cache) {
+                    if (acquire_dep(args, dep) < 0) {
+                        if (lane == 0) s_abort = 1;
+                        g = total;
+                    } else {
+                        cache = dep;
+                        fresh = true;
+                    }
+                }
             }
-            if (lane == 0) s_info[b] = g;
             if (g >= total) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[b]);        // no data: consumers see the end
+                // end marker for this group; then one for the other group
+                if (lane == 0) {
+                    s_info[b] = total;
+                    mbar_arrive(&posted[b]);
+                    mbar_arrive(&full[b]);
+                    mbar_arrive(&full[b]);
+                }
+                if (++ends == 2) break;
+                continue;
+            }
+            if (lane == 0) {
+                s_info[b] = g;
+                mbar_arrive(&posted[b]);                      // the table warp may start
+                if (fresh) fence_async_global();              // panel data of other CTAs, then TMA reads
+                fence_async_shared();                         // consumers' accesses of stage b, then TMA writes
+                issue_loads<MODE, B2>(args, d, stage + b * TILE_BYTES, &full[b]);
+            }
+        }
+        // Iterations i-1 and i posted the end markers on stages whose earlier
+        // loads had been consumed.  The loads of iterations i-NSTAGE+1 .. i-2
+        // may still be in flight: wait (bounded) for them before exiting.  No
+        // later phase was posted on their stages, so each parity names the
+        // current or the just-completed phase.
+        if (lane == 0)
+            for (int j = (i - NSTAGE + 1 < 0 ? 0 : i - NSTAGE + 1); j < i - 1; ++j)
+                mbar_wait(&full[j % NSTAGE], (unsigned)((j / NSTAGE) & 1), WAIT_NS);
+        return;
+    }
+    if (warp == NCW + 2) {
+        // ---------------- twiddle tables ----------------
+        for (int i = 0;; ++i) {
+            const int b = i % NSTAGE;
+            const int ok = mbar_wait(&posted[b], (unsigned)((i / NSTAGE) & 1), WAIT_NS);   // every lane
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) { s_abort = 1; atomicExch(args.status, 5); }
                 break;
             }
-            build_tables(args, d, TWs[b], E1s[b], E2s[b], w128, tlo);
-            __syncwarp();                                    // tables written before the arrive
-            fence_async_global();                            // scratch written by other CTAs, then read by TMA
-            fence_async_shared();                            // consumers' reads of stage b, then TMA writes
-            issue_tile(args, d, stage + b * STAGE_ELEMS, &full[b]);
+            const int g = s_info[b];
+            if (g >= total) break;
+            build_tables<MODE>(args, decode_tile(g, lgT, args.npanels), TWs[b], E1s[b], E2s[b], tlo, w128);
+            __syncwarp();                                     // tables written before the arrive
+            if (lane == 0) mbar_arrive(&full[b]);
+        }
+        return;
+    }
+    if (warp == NCW + 1) {
+        // ---------------- storer ----------------
+        if (lane == 0) {
+            StorerState st;
+            st.last_b = -1;
+            st.pa = nullptr; st.na = 0; st.pa_async = 0;
+            st.pb = nullptr; st.nb = 0;
+            for (int i = 0;; ++i) {
+                const int b = i % NSTAGE;
+                const unsigned par = (unsigned)((i / NSTAGE) & 1);
+                if (!mbar_test(&done[b], par)) {
+                    storer_flush(st, empty);
+                    if (!mbar_wait(&done[b], par, WAIT_NS)) {
+                        s_abort = 1;
+                        atomicExch(args.status, 5);
+                        break;
+                    }
+                }
+                const int g = s_info[b];
+                if (g >= total) break;
+                const Tile d = decode_tile(g, lgT, args.npanels);
+                unsigned *ctr = tile_ctr(args, d);
+                if (!d.isB) {
+                    if (st.pa != ctr) storer_release_a(st);
+                    st.pa = ctr;
+                    ++st.na;
+                } else {
+                    if (st.pb != ctr) storer_release_b(st);
+                    st.pb = ctr;
+                    ++st.nb;
+                }
+                if (!d.isB && MODE == 1) {
+                    // the consumers stored this tile to the panel buffer themselves
+                    mbar_arrive(&empty[b]);
+                    continue;
+                }
+                const int bidx = d.q >> args.lgPpb, pcol = d.q & (args.panels_per_batch - 1);
+                const int colbase = pcol << args.lgP;
+                const int hi = tile_hi(args, d, MODE), lo = tile_lo32(args, d, MODE);
+                const unsigned char *src = stage + b * TILE_BYTES;
+                if (!d.isB) {
+                    st.pa_async = 1;
+                    const unsigned long long pol = policy_evict_last();
+#pragma unroll
+                    for (int x = 0; x < NBOX; ++x)
+                        tma_st_3d(&args.map_scr_st, lo + 16 * x, hi, (d.q % NBUF) * 128, src + x * BOX_BYTES, pol);
+                } else if (MODE == 1) {
+                    const unsigned long long pol = policy_evict_first();
+                    const unsigned u = digit_reverse((unsigned)(colbase + hi), args.rev_bits, args.rev_t);
+                    const int row = (int)u + bidx * args.N2rows;
+#pragma unroll
+                    for (int x = 0; x < NBOX; ++x)
+                        tma_st_3d(&args.map_out, lo + 16 * x, 0, row, src + x * BOX_BYTES, pol);
+                } else {
+                    const unsigned long long pol = policy_evict_first();
+#pragma unroll
+                    for (int x = 0; x < NBOX; ++x)
+                        tma_st_3d(&args.map_out, colbase + lo + 16 * x, hi, bidx * 128, src + x * BOX_BYTES, pol);
+                }
+                bulk_commit();
+                if (st.last_b >= 0) {                         // the previous group has read its stage
+                    bulk_wait_read1();
+                    mbar_arrive(&empty[st.last_b]);
+                }
+                st.last_b = b;
+            }
+            storer_flush(st, empty);
+            bulk_wait0();
         }
         return;
     }
 
     // ---------------- consumer warps ----------------
-    unsigned fparity = 0;
-    cx<float> v[16];
-    for (int i = 0;; ++i) {
+    const unsigned stage_base = smem_u32(stage);
+    for (int i = warp / WPG;; i += 2) {
         const int b = i % NSTAGE;
-        float2 *sbuf = stage + b * STAGE_ELEMS;
-        if (!mbar_wait(&full[b], (fparity >> b) & 1u, 1u << 22)) s_abort = 1;
-        fparity ^= 1u << b;
-        const int g = s_info[b];                             // the same for every consumer
-        if (g >= total) break;
-        const Tile d = decode_tile(g, lgT, args.npanels);
-        if (d.isB) discard_consumed(args, d);
-        read_landing(args, d, v, sbuf, lrow);
-        int t8, slot;
-        pass1_regs(args, d, v, w16, t8, slot);
-        named_barrier_consumers();                           // landing reads done
-#pragma unroll
-        for (int s = 0; s < 16; ++s) sbuf[(t8 + 8 * s) * SP + slot] = make_float2(v[s].x, v[s].y);
-        named_barrier_consumers();                           // exchange written
-        pass2_store(args, d, v, sbuf, TWs[b], E1s[b], E2s[b]);
-        named_barrier_consumers();                           // stage b free; stores issued
-        if (tid == 0) {
-            red_release_add(args.ctr + 1 + (d.isB ? args.npanels : 0) + d.q, 1u);
-            mbar_arrive(&empty[b]);
+        const int ok = mbar_wait(&full[b], (unsigned)((i / NSTAGE) & 1), WAIT_NS);   // every lane
+        if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) { s_abort = 1; atomicExch(args.status, 5); }
+            break;
         }
+        const int g = s_info[b];
+        if (g >= total) {
+            if (lane == 0) mbar_arrive(&done[b]);
+            break;
+        }
+        const Tile d = decode_tile(g, lgT, args.npanels);
+        if (d.isB) {
+            // drop the consumed panel lines (now in shared memory): one 128-byte
+            // box row per lane, rows 32 (wl & 3) + lane of box wl >> 2
+            const int hi = tile_hi(args, d, MODE), lo = tile_lo32(args, d, MODE);
+            const int wl = warp & (WPG - 1);
+            const int bx = wl >> 2, row = 32 * (wl & 3) + lane;
+            const float2 *sc = reinterpret_cast<const float2 *>(args.scratch);
+            const size_t slot = (size_t)(d.q % NBUF);
+            const float2 *line = (MODE == 1)
+                ? sc + (((slot << args.lgP) + (size_t)hi) * 128 + (size_t)row) * 128 + lo + 16 * bx
+                : sc + ((slot * 128 + (size_t)hi) * 128 + (size_t)row) * (size_t)args.P + lo + 16 * bx;
+            discard_l2(line);
+        }
+        consume_tile<MODE, B2>(args, d, stage_base + (unsigned)b * TILE_BYTES, TWs[b], E1s[b], E2s[b], w16);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&done[b]);
     }
 }
 

@@ -174,3 +174,300 @@ def test_tensor_core_fragment_mapping():
                     n = 8 * nt + 2 * q + h
                     Y[n, g + 8 * si] = acc[nt, 0, lane, h + 2 * si] + 1j * acc[nt, 1, lane, h + 2 * si]
     assert np.allclose(Y, np.fft.fft(V, axis=1))
+
+
+# ---------------------------------------------------------------------------
+# The 2^14 panel pipeline (paco_panel.cuh): one tile of each kind
+# ---------------------------------------------------------------------------
+
+def _swz(addr):
+    """TMA 128-byte swizzle of a byte offset inside a 1024-aligned buffer:
+    the 16-byte chunk index (bits 4-6) is XORed with the row index mod 8
+    (bits 7-9)."""
+    return addr ^ (((addr >> 7) & 7) << 4)
+
+
+def _tma_box(box_dims, coord_to_global):
+    """Yield (smem byte offset, global index) of every element of a box, the
+    first dimension fastest (8-byte elements, 128-byte swizzle)."""
+    idx = np.indices(box_dims[::-1]).reshape(len(box_dims), -1)[::-1]   # idx[0] fastest
+    lin = np.zeros(idx.shape[1], dtype=np.int64)
+    mul = 1
+    for k, d in enumerate(box_dims):
+        lin += idx[k] * mul
+        mul *= d
+    return _swz(lin * 8), coord_to_global(*idx)
+
+
+def land_lo(b, t8):
+    return (((t8 & 1) << 2) | (t8 & 2) | ((t8 >> 2) & 1)) if b == 2 else t8
+
+
+def land_hi(b, s):
+    if b == 2:
+        return ((s & 1) << 3) | ((s & 2) << 1) | ((s >> 1) & 2) | ((s >> 3) & 1)
+    if b == 4:
+        return ((s & 3) << 2) | ((s >> 2) & 3)
+    return s
+
+
+NBOX = 2            # TMA boxes (16 sequences x 128 points) per tile
+WPG = 8             # consumer warps per tile (one group)
+
+
+def _lane(warp, lane):
+    """(q, column, chunk, half, box byte offset) of lane `lane` of consumer
+    warp `warp` (0..7 within its group)."""
+    q = lane & 7
+    col = 4 * (warp & 3) + (lane >> 3)
+    cc, half = col >> 1, col & 1
+    return q, col, cc, half, (warp >> 2) * 16384 + half * 8
+
+
+def _consume(smem, kind, b, conj, TW=None, E1=None, E2=None):
+    """The consumer warps of paco_panel_kernel on one landed tile, with the
+    kernel's address formulas.  `smem` is the 32 KiB stage buffer as 4096
+    complex slots (byte offset / 8).  Returns the per-lane outputs for the
+    stage-1 A 16-byte stores as {(warp, lane, k8): (y_h0, y_h1)} and writes the
+    in-place store image into smem for the other kinds."""
+    w128 = np.exp(-2j * np.pi * np.arange(128) / 128)
+    paired = (kind == "1A")
+    stores = {}
+    reads, writes = set(), set()
+    new = {}
+    for warp in range(WPG):
+        for lane in range(32):
+            q, col, cc, half, box = _lane(warp, lane)
+            stage2A = (kind == "2A")
+            lo = land_lo(b, q) if stage2A else q
+            base = box + (lo << 7) + ((cc ^ lo) << 4)
+            v = np.array([smem[(base + (land_hi(b, s) if stage2A else s) * 1024) // 8] for s in range(16)])
+            for s in range(16):
+                reads.add(base + (land_hi(b, s) if stage2A else s) * 1024)
+            if kind in ("1A", "2A") and conj:
+                v = np.conj(v)
+            v = np.fft.fft(v)
+            v = v * w128[(np.arange(16) * q) % 128]
+            e0 = box + (q << 7) + ((cc ^ q) << 4)
+            for k in range(16):
+                m = (k >> 1) if paired else (k & 7)
+                a = (e0 ^ (m * 0x90)) + k * 1024
+                writes.add(a)
+                new.setdefault(("x", a), v[k])
+            stores[(warp, lane)] = e0
+    # exchange: every lane of a warp writes before any lane reads (__syncwarp)
+    assert len(writes) == WPG * 32 * 16 and writes == reads    # in place, bijective
+    for (_, a), val in new.items():
+        smem[a // 8] = val
+    out = {}
+    images = {}
+    kb0 = lambda q: 2 * q if paired else q
+    kbs = 1 if paired else 8
+    for warp in range(WPG):
+        for lane in range(32):
+            e0 = stores[(warp, lane)]
+            q, col, cc, half, box = _lane(warp, lane)
+            rb = e0 + (q * 2048 if paired else q * 1024)
+            hs = 1024 if paired else 8192
+            res = np.zeros(16, complex)
+            for h in range(2):
+                xs = np.array([smem[((rb ^ (t * 0x90)) + h * hs) // 8] for t in range(8)])
+                res[8 * h:8 * h + 8] = np.fft.fft(xs)
+            k = np.array([kb0(q) + kbs * h + 16 * k8 for h in range(2) for k8 in range(8)])
+            if kind in ("1A", "2A"):
+                res = res * TW[k]
+            elif kind == "1B":
+                res = res * E1[16 * (warp >> 2) + col] * E2[k]
+            if kind in ("1B", "2B") and conj:
+                res = np.conj(res)
+            if paired:
+                for k8 in range(8):
+                    out[(warp, lane, k8)] = (res[k8], res[8 + k8])
+            else:
+                ob = box + (q << 7) + ((cc ^ q) << 4)
+                for h in range(2):
+                    for k8 in range(8):
+                        a = ob + h * 1024 + k8 * 2048
+                        assert (a % 16384) // 128 == k[8 * h + k8]   # image row = output index
+                        images[a] = res[8 * h + k8]
+    if not paired:
+        assert len(images) == 4096
+        for a, val in images.items():
+            smem[a // 8] = val
+    return out
+
+
+@pytest.mark.parametrize("conj", [False, True])
+def test_panel_stage1_tiles_model(conj):
+    """Stage 1 (N1 = 2^14 rows, C = 256 columns, P = 128): an A tile (TMA
+    box (16 c, 1 j_lo, 128 j_hi)) through the consumers to the panel buffer
+    [c][j_lo][k_lo] (16-byte stores), then a B tile of that panel buffer
+    (box (16 k_lo, 128 j_lo, 1 c)) to W's row pi(c) (box (16 k_lo, 128 k_hi)):
+    every value lands where the two-factor DFT, the twiddle w_L^{-k_lo j_lo}
+    and the epilogue w_N^{-k1 c} put it."""
+    rng = np.random.default_rng(1)
+    L, C, P = 16384, 256, 128
+    N = L * C
+    X = rng.standard_normal((L, C)) + 1j * rng.standard_normal((L, C))
+    wL = np.exp(-2j * np.pi * np.arange(L) / L)
+    q_panel, slot = 1, 1
+    colbase = q_panel * P
+    # --- A tile t: j_lo = t >> 2, columns c0 = 32 (t & 3)
+    t = 77
+    jlo, c0 = t >> 2, 32 * (t & 3)
+    smem = np.full(4096, np.nan, complex)
+    for x in range(NBOX):
+        offs, (cg, jl, jh) = _tma_box((16, 1, 128), lambda a, bb, c: (colbase + c0 + 16 * x + a, jlo + bb, c))
+        smem[(x * 16384 + offs) // 8] = X[jl + 128 * jh, cg]
+    TW = wL[(np.arange(128) * jlo) % L]
+    out = _consume(smem, "1A", 2, conj, TW=TW)
+    scratch = {}
+    for (warp, lane, k8), (y0, y1) in out.items():
+        q, col, _, _, _ = _lane(warp, lane)
+        cl = c0 + 16 * (warp >> 2) + col
+        base = ((slot * P + cl) * 128 + jlo) * 128 + 2 * q + 16 * k8
+        scratch[base] = y0
+        scratch[base + 1] = y1
+    # dir = +1 conjugates on the A tile's load and on the B tile's store:
+    # between the two the panel buffer holds the forward transform of conj(x)
+    xc = np.conj(X) if conj else X
+    for cl in range(c0, c0 + 32):
+        seq = xc[jlo + 128 * np.arange(128), colbase + cl]
+        want = np.fft.fft(seq) * TW
+        got = np.array([scratch[((slot * P + cl) * 128 + jlo) * 128 + k] for k in range(128)])
+        assert np.allclose(got, want)
+    # --- B tile: column cl, k0 = 32 (t & 3); its panel buffer filled with the true A results
+    cl, k0 = 93, 64
+    cglob = colbase + cl
+    Acol = np.array([np.fft.fft(xc[jl + 128 * np.arange(128), cglob]) * wL[(np.arange(128) * jl) % L]
+                     for jl in range(128)])                    # [j_lo][k_lo]
+    smem = np.full(4096, np.nan, complex)
+    for x in range(NBOX):
+        offs, (kl, jl, c) = _tma_box((16, 128, 1), lambda a, bb, c: (k0 + 16 * x + a, bb, c))
+        smem[(x * 16384 + offs) // 8] = Acol[jl, kl]
+    E1 = np.exp(-2j * np.pi * (((k0 + np.arange(32)) * cglob) % N) / N)
+    E2 = np.exp(-2j * np.pi * ((128 * np.arange(128) * cglob) % N) / N)
+    _consume(smem, "1B", 2, conj, E1=E1, E2=E2)
+    Wrow = {}
+    for x in range(NBOX):
+        offs, (kl, kh, _) = _tma_box((16, 128, 1), lambda a, bb, c: (k0 + 16 * x + a, bb, c))
+        for o, a_, b_ in zip(offs, kl, kh):
+            Wrow[a_ + 128 * b_] = smem[(x * 16384 + o) // 8]
+    # Z[k1, c] = A[k1, c] w_N^{-k1 c} for the 32 k_lo of the tile, all k_hi
+    # (for dir = +1: the conjugate of that product formed on conj(x))
+    full = np.fft.fft(xc[:, cglob])
+    assert len(Wrow) == 32 * 128
+    for k1, got in Wrow.items():
+        want = full[k1] * np.exp(-2j * np.pi * ((k1 * cglob) % N) / N)
+        if conj:
+            want = np.conj(want)
+        assert abs(got - want) < 1e-9 * np.sqrt(L) * 10, (k1, got, want)
+
+
+@pytest.mark.parametrize("b", [2, 4])
+@pytest.mark.parametrize("conj", [False, True])
+def test_panel_stage2_tiles_model(b, conj):
+    """Stage 2 (W with N2 = 2^14 rows, C = 128 columns, P = 128): an A tile
+    loads rows pi(j_lo + 128 j_hi) through the tensor map whose row dimensions
+    are ordered as in panel_prepare (b = 2: rank 4; b = 4: rank 5 plus the
+    second map for row bit 6) -- the landing order the consumers assume
+    (land_lo, land_hi) must give logical j_hi = t8 + 8 s in v[s] -- and is
+    stored to the panel buffer [k_lo][j_lo][v]; a B tile of that buffer is
+    stored to Y (box (16 v, 1 k_lo, 128 k_hi)).  Values must land where the
+    length-2^14 DFT over the digit-reversed rows puts them."""
+    import oracle
+    rng = np.random.default_rng(2)
+    L, C, P = 16384, 128, 128
+    t = 2 if b == 4 else 1
+    pi = oracle.digit_reverse_table(b, 14 // t)
+    W = rng.standard_normal((L, C)) + 1j * rng.standard_normal((L, C))
+    wL = np.exp(-2j * np.pi * np.arange(L) / L)
+    # --- A tile: j_lo, 64 columns v0
+    for jlo in (0, 37, 64 + 5):
+        v0 = 96
+        u = int(pi[jlo])
+        smem = np.full(4096, np.nan, complex)
+        for x in range(NBOX):
+            if b == 2:
+                f = lambda vv, d1, d2, d3: (v0 + 16 * x + vv, d1 * 16 + d2 + 128 * (d3 + (u >> 7)))
+                offs, (vg, row) = _tma_box((16, 8, 16, 1), f)
+            else:
+                base_row = 64 if (u >> 6) & 1 else 0
+                f = lambda vv, d1, d2, d3, d4: (v0 + 16 * x + vv,
+                                                base_row + 128 * d1 + 16 * d2 + d3 + 256 * (d4 + (u >> 8)))
+                offs, (vg, row) = _tma_box((16, 2, 4, 16, 1), f)
+            smem[(x * 16384 + offs) // 8] = W[row, vg]
+        TW = wL[(np.arange(128) * jlo) % L]
+        _consume(smem, "2A", b, conj, TW=TW)
+        for x in range(NBOX):
+            offs, (vv, jl, kl) = _tma_box((16, 1, 128), lambda a, bb, c: (v0 + 16 * x + a, jlo + bb, c))
+            for o, vg, k in zip(offs, vv, kl):
+                seq = W[pi[jlo + 128 * np.arange(128)], vg]
+                want = np.fft.fft(np.conj(seq) if conj else seq)[k] * TW[k]
+                assert abs(smem[(x * 16384 + o) // 8] - want) < 1e-9, (jlo, vg, k)
+    # --- B tile: k_lo, 64 columns v0 over a panel buffer [k_lo][j_lo][v]
+    klo, v0 = 21, 32
+    logical = W[pi, :]                                     # logical rows j
+    lc = np.conj(logical) if conj else logical             # dir = +1: conjugated on the A load
+    Aall = np.empty((128, 128, C), complex)                # [k_lo][j_lo][v]
+    for jl in range(128):
+        seqs = lc[jl + 128 * np.arange(128), :]            # (j_hi, v)
+        Aall[:, jl, :] = np.fft.fft(seqs, axis=0) * wL[(np.arange(128) * jl) % L][:, None]
+    smem = np.full(4096, np.nan, complex)
+    for x in range(NBOX):
+        offs, (vv, jl, kl) = _tma_box((16, 128, 1), lambda a, bb, c: (v0 + 16 * x + a, bb, klo + c))
+        smem[(x * 16384 + offs) // 8] = Aall[kl, jl, vv]
+    _consume(smem, "2B", b, conj)
+    Yfull = np.fft.fft(lc, axis=0)
+    if conj:
+        Yfull = np.conj(Yfull)
+    for x in range(NBOX):
+        offs, (vv, kl, kh) = _tma_box((16, 1, 128), lambda a, bb, c: (v0 + 16 * x + a, klo + bb, c))
+        for o, vg, k_lo, k_hi in zip(offs, vv, kl, kh):
+            want = Yfull[k_lo + 128 * k_hi, vg]
+            assert abs(smem[(x * 16384 + o) // 8] - want) < 1e-9 * 128, (vg, k_lo, k_hi)
+
+
+def test_panel_shared_accesses_are_conflict_free():
+    """Every shared-memory access instruction of a consumer warp (landing
+    reads for each tile kind and b, both sides of the exchange in its paired
+    and staged forms, the store image) is served without bank conflicts: an
+    8-byte access is served per half-warp, and each half-warp's 16 lanes must
+    touch each of the 32 four-byte banks exactly once."""
+    def conflict_free(addrs):
+        for hw in (addrs[:16], addrs[16:]):
+            cnt = np.zeros(32, int)
+            for a in hw:
+                for w in range(2):
+                    cnt[((a + 4 * w) // 4) % 32] += 1
+            if cnt.max() != 1:
+                return False
+        return True
+
+    def lanes(f):
+        return [f(*_lane(warp, lane)) for lane in range(32)]
+
+    for warp in range(WPG):
+        for kind, b in (("A1", 2), ("A2", 2), ("A2", 4), ("B", 2)):
+            for s in range(16):
+                def f(q, col, cc, half, box, s=s):
+                    lo = land_lo(b, q) if kind == "A2" else q
+                    hs = land_hi(b, s) if kind == "A2" else s
+                    return box + (lo << 7) + ((cc ^ lo) << 4) + hs * 1024
+                assert conflict_free(lanes(f)), (kind, b, s)
+        for paired in (True, False):
+            for k in range(16):
+                m = (k >> 1) if paired else (k & 7)
+                assert conflict_free(lanes(lambda q, col, cc, half, box:
+                                           ((box + (q << 7) + ((cc ^ q) << 4)) ^ (m * 0x90)) + k * 1024))
+            for h in range(2):
+                for tt in range(8):
+                    def f(q, col, cc, half, box):
+                        e0 = box + (q << 7) + ((cc ^ q) << 4)
+                        rb = e0 + (q * 2048 if paired else q * 1024)
+                        return (rb ^ (tt * 0x90)) + h * (1024 if paired else 8192)
+                    assert conflict_free(lanes(f)), (paired, h, tt)
+        for h in range(2):
+            for k8 in range(8):
+                assert conflict_free(lanes(lambda q, col, cc, half, box:
+                                           box + (q << 7) + ((cc ^ q) << 4) + h * 1024 + k8 * 2048))
