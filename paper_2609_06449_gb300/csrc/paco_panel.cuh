@@ -36,10 +36,12 @@
 //     results are written back in place (or, for stage-1 A tiles, stored to
 //     the panel buffer with 16-byte stores);
 //   * a storer warp writes each finished tile out with two TMA tensor stores
-//     (one store group in flight), returns stage buffers to the producer once
-//     the stores have read them, and publishes the panel counters in batches
-//     (a release per run of tiles of one counter, and before every wait, so
-//     no CTA holds back a count another CTA waits for while it is idle).
+//     (one store group in flight) and returns stage buffers to the producer
+//     once the stores have read them;
+//   * a publisher warp makes the completed tiles count: the storer hands it
+//     each completion through a shared-memory ring, and it publishes them to
+//     the panel counters other CTAs wait on, one GPU-scope fence per batch
+//     (the fence is the costly part, so it stays off the storer's path).
 // The 128-byte swizzle makes every shared-memory access of a warp (landing
 // reads, both sides of the exchange, the output staging) conflict-free.
 #pragma once
@@ -92,7 +94,8 @@ namespace panel {
 constexpr int A = 128, B = 128, L = A * B;
 constexpr int NCW = 16;                  // consumer warps
 constexpr int WPG = 8;                   // consumer warps per group (one tile)
-constexpr int NT = (NCW + 3) * 32;       // + producer, storer and table warps
+constexpr int NT = (NCW + 4) * 32;       // + producer, storer, table and publisher warps
+constexpr int PQ = 64;                   // completions the storer may hand the publisher at once
 constexpr int TILE = 4096;               // elements per tile (32 sequences x 128)
 constexpr int NBOX = 2;                  // TMA boxes per tile
 constexpr int NBUF = 3;                  // panel buffers in the L2 ring
@@ -126,10 +129,6 @@ __device__ __forceinline__ void st_v4_hint(void *p, float4 v, unsigned long long
 {
     asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
                  :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(pol) : "memory");
-}
-__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ void red_relaxed_add(unsigned *p, unsigned v)
 {
@@ -236,6 +235,7 @@ __device__ __forceinline__ void tma_st_3d(const CUtensorMap *map, int c0, int c1
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait1() { asm volatile("cp.async.bulk.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
@@ -548,60 +548,46 @@ __device__ __forceinline__ void consume_tile(const PanelArgs &a, const Tile &d, 
     }
 }
 
-// ---- storer ------------------------------------------------------------------
+// ---- storer -> publisher ring -------------------------------------------------
 
-// The storer's outstanding work: the stage whose store group is the newest
-// (its reads not yet confirmed) and the counter increments not yet published.
-struct StorerState {
-    int last_b;                    // stage of the newest store group, -1: none
-    unsigned *pa; unsigned na;     // pending completions of A tiles (panel counter, count)
-    int pa_async;                  // those A tiles were stored by TMA: publish after their writes
-    unsigned *pb; unsigned nb;     // pending completions of B tiles
+// Completed tiles travel from the storer to the publisher as pointers to the
+// counter they count towards; bit 0 set: the tile was written by TMA stores
+// (the publisher orders those writes before its release with a proxy fence).
+struct PubRing {
+    unsigned long long slot[panel::PQ];
+    int tail;                      // entries appended (storer)
+    int head;                      // entries published (publisher)
+    int fin;                       // the storer appends no more
 };
 
-__device__ __forceinline__ void storer_release_a(StorerState &st)
+__device__ __forceinline__ int ld_acquire_cta(const int *p)
 {
-    if (!st.pa) return;
-    if (st.pa_async) {
-        panel::bulk_wait0();                                  // the stores are written
-        panel::fence_async_global();
-    }
-    panel::red_release_add(st.pa, st.na);
-    st.pa = nullptr;
-    st.na = 0;
-    st.pa_async = 0;
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(panel::smem_u32(p)) : "memory");
+    return v;
 }
-__device__ __forceinline__ void storer_release_b(StorerState &st)
+__device__ __forceinline__ void st_release_cta(int *p, int v)
 {
-    if (!st.pb) return;
-    panel::red_release_add(st.pb, st.nb);
-    st.pb = nullptr;
-    st.nb = 0;
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" :: "r"(panel::smem_u32(p)), "r"(v) : "memory");
 }
-// Everything outstanding: before the storer blocks, so that no count another
-// CTA (or this CTA's producer) waits for is held back by an idle storer.
-__device__ __forceinline__ void storer_flush(StorerState &st, unsigned long long *empty)
+
+// Storer side: append one completion (bounded wait while the ring is full).
+__device__ __forceinline__ void pub_push(PubRing &r, int &tail, unsigned *ctr, int async, int *status)
 {
-    if (st.last_b >= 0) {
-        panel::bulk_wait_read0();
-        panel::mbar_arrive(&empty[st.last_b]);
-        st.last_b = -1;
+    if (tail - ld_acquire_cta(&r.head) >= panel::PQ) {
+        const unsigned long long t0 = panel::global_ns();
+        while (tail - ld_acquire_cta(&r.head) >= panel::PQ) {
+            if (panel::global_ns() - t0 > panel::WAIT_NS) { atomicExch(status, 5); return; }
+            __nanosleep(200);
+        }
     }
-    if (!st.pa && !st.pb) return;
-    if (st.pa && st.pa_async) {
-        panel::bulk_wait0();                                  // the stores are written
-        panel::fence_async_global();
-    }
-    panel::fence_acq_rel_gpu();                               // one fence publishes both counts
-    if (st.pa) panel::red_relaxed_add(st.pa, st.na);
-    if (st.pb) panel::red_relaxed_add(st.pb, st.nb);
-    st.pa = st.pb = nullptr;
-    st.na = st.nb = 0;
-    st.pa_async = 0;
+    r.slot[tail % panel::PQ] = (unsigned long long)ctr | (unsigned long long)async;
+    st_release_cta(&r.tail, ++tail);
 }
 
 // Warps 0..15 consume (groups 0 and 1 take even and odd tiles), warp 16
-// produces, warp 17 stores, warp 18 builds the twiddle tables.
+// produces, warp 17 stores, warp 18 builds the twiddle tables, warp 19
+// publishes the completions.
 template <int MODE, int B2>
 __global__ void __launch_bounds__(panel::NT, 1)
     paco_panel_kernel(const __grid_constant__ PanelArgs args)
@@ -614,6 +600,7 @@ __global__ void __launch_bounds__(panel::NT, 1)
     __shared__ float2 TWs[NSTAGE][128];                   // per-stage w_L table (A tiles)
     __shared__ float2 E1s[NSTAGE][32], E2s[NSTAGE][B];    // per-stage w_N factors (stage-1 B)
     __shared__ int s_info[NSTAGE];                        // tile index held by each stage
+    __shared__ PubRing ring;
     __shared__ volatile int s_abort;
 
     // the dynamic buffer starts 1024-aligned (the 128-byte swizzle needs it)
@@ -634,6 +621,7 @@ __global__ void __launch_bounds__(panel::NT, 1)
 
         }
         s_abort = 0;
+        ring.tail = ring.head = ring.fin = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     const int lgT = args.lgP + 2;                        // T = 4 P tiles per phase
@@ -727,15 +715,25 @@ __global__ void __launch_bounds__(panel::NT, 1)
     if (warp == NCW + 1) {
         // ---------------- storer ----------------
         if (lane == 0) {
-            StorerState st;
-            st.last_b = -1;
-            st.pa = nullptr; st.na = 0; st.pa_async = 0;
-            st.pb = nullptr; st.nb = 0;
+            int tail = 0;
+            int last_b = -1;                                  // stage of the newest store group
+            unsigned *last_a = nullptr;                       // its A-tile counter (stage 2), if any
             for (int i = 0;; ++i) {
                 const int b = i % NSTAGE;
                 const unsigned par = (unsigned)((i / NSTAGE) & 1);
                 if (!mbar_test(&done[b], par)) {
-                    storer_flush(st, empty);
+                    // about to wait: nothing stays held back meanwhile (the stage
+                    // returns once the stores have read it; an A tile counts once written)
+                    if (last_b >= 0) {
+                        bulk_wait_read0();
+                        mbar_arrive(&empty[last_b]);
+                        if (last_a) {
+                            bulk_wait0();
+                            pub_push(ring, tail, last_a, 1, args.status);
+                        }
+                        last_b = -1;
+                        last_a = nullptr;
+                    }
                     if (!mbar_wait(&done[b], par, WAIT_NS)) {
                         s_abort = 1;
                         atomicExch(args.status, 5);
@@ -746,26 +744,18 @@ __global__ void __launch_bounds__(panel::NT, 1)
                 if (g >= total) break;
                 const Tile d = decode_tile(g, lgT, args.npanels);
                 unsigned *ctr = tile_ctr(args, d);
-                if (!d.isB) {
-                    if (st.pa != ctr) storer_release_a(st);
-                    st.pa = ctr;
-                    ++st.na;
-                } else {
-                    if (st.pb != ctr) storer_release_b(st);
-                    st.pb = ctr;
-                    ++st.nb;
-                }
                 if (!d.isB && MODE == 1) {
                     // the consumers stored this tile to the panel buffer themselves
+                    pub_push(ring, tail, ctr, 0, args.status);
                     mbar_arrive(&empty[b]);
                     continue;
                 }
+                if (d.isB) pub_push(ring, tail, ctr, 0, args.status);   // its panel lines were read
                 const int bidx = d.q >> args.lgPpb, pcol = d.q & (args.panels_per_batch - 1);
                 const int colbase = pcol << args.lgP;
                 const int hi = tile_hi(args, d, MODE), lo = tile_lo32(args, d, MODE);
                 const unsigned char *src = stage + b * TILE_BYTES;
                 if (!d.isB) {
-                    st.pa_async = 1;
                     const unsigned long long pol = policy_evict_last();
 #pragma unroll
                     for (int x = 0; x < NBOX; ++x)
@@ -784,14 +774,64 @@ __global__ void __launch_bounds__(panel::NT, 1)
                         tma_st_3d(&args.map_out, colbase + lo + 16 * x, hi, bidx * 128, src + x * BOX_BYTES, pol);
                 }
                 bulk_commit();
-                if (st.last_b >= 0) {                         // the previous group has read its stage
+                if (last_b >= 0) {
+                    // the previous group has read its stage; an A tile's completion
+                    // is published once its stores are written
                     bulk_wait_read1();
-                    mbar_arrive(&empty[st.last_b]);
+                    mbar_arrive(&empty[last_b]);
+                    if (last_a) {
+                        bulk_wait1();
+                        pub_push(ring, tail, last_a, 1, args.status);
+                    }
                 }
-                st.last_b = b;
+                last_b = b;
+                last_a = d.isB ? nullptr : ctr;
             }
-            storer_flush(st, empty);
             bulk_wait0();
+            if (last_b >= 0) {
+                mbar_arrive(&empty[last_b]);
+                if (last_a) pub_push(ring, tail, last_a, 1, args.status);
+            }
+            st_release_cta(&ring.fin, 1);
+        }
+        return;
+    }
+    if (warp == NCW + 3) {
+        // ---------------- publisher ----------------
+        if (lane == 0) {
+            int head = 0;
+            unsigned long long idle_since = 0;
+            for (;;) {
+                const int fin = ld_acquire_cta(&ring.fin);
+                const int tail = ld_acquire_cta(&ring.tail);
+                if (tail == head) {
+                    if (fin) break;
+                    const unsigned long long now = global_ns();
+                    if (!idle_since) idle_since = now;
+                    else if (now - idle_since > 2 * WAIT_NS) break;   // the storer gave up
+                    __nanosleep(256);
+                    continue;
+                }
+                idle_since = 0;
+                int async = 0;
+                for (int k = head; k < tail; ++k) async |= (int)(ring.slot[k % PQ] & 1ull);
+                if (async) fence_async_global();              // TMA-stored panel data, then the release
+                fence_acq_rel_gpu();                          // one fence publishes the batch
+                unsigned *run = nullptr;
+                unsigned n = 0;
+                for (int k = head; k < tail; ++k) {
+                    unsigned *c = reinterpret_cast<unsigned *>(ring.slot[k % PQ] & ~1ull);
+                    if (c != run) {
+                        if (run) red_relaxed_add(run, n);
+                        run = c;
+                        n = 0;
+                    }
+                    ++n;
+                }
+                if (run) red_relaxed_add(run, n);
+                head = tail;
+                st_release_cta(&ring.head, head);
+            }
         }
         return;
     }
