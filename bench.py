@@ -292,6 +292,21 @@ def captured_traffic(stage: str, N1: int, N2: int, b: int, p: int, dtype: str, d
         return None
 
 
+def fp64_peak_measured(paco, gpu_index: int):
+    """The FP64 FMA rate of this GPU, measured by the library's DFMA probe
+    (paco_probe_fp64_peak: one launch, CUDA events) with the SM clock sampled
+    while it runs; returns (GFLOP/s, description)."""
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.time()
+    g, ms = paco.probe_fp64_peak(iters=8192)
+    t1 = time.time()
+    clk = sampler.stop(t0, t1)
+    return g, (f"measured: DFMA probe (paco_probe_fp64_peak), {ms:.1f} ms at a median SM clock of "
+               f"{clk.get('sm_mhz')} MHz (max {clk.get('sm_max_mhz')} MHz), FMA = 2 flops")
+
+
 def measured_peak_hbm():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -466,6 +481,7 @@ def run_other(args, ranks, local):
         N1 = N2 = 256
         N = N1 * N2
         plan = paco.Plan(N1, N2, 2, 1, paco.C64, p=4)
+        fused = bool(plan.info.fused_cluster)
         xh = torch.from_numpy(uniform(N, rank, np.complex64)).pin_memory()
         x = xh.cuda()
         y = torch.empty_like(x)
@@ -487,10 +503,13 @@ def run_other(args, ranks, local):
                             "N1": N1, "N2": N2, "b": 2, "p": 4, "batch": 1,
                             "input": "Re, Im i.i.d. U[-1,1), seed = rank",
                             "l2": "input fits in L2: latency-bound by design, no flush"},
-                    roofline=dict(hbm_roofline("stage kernels (2 launches)", 32.0 * N, statistics.median(per)),
+                    roofline=dict(hbm_roofline("paco_cluster_kernel (one launch, 16-CTA cluster)" if fused
+                                               else "stage kernels (2 launches)",
+                                               (16.0 if fused else 32.0) * N, statistics.median(per)),
                                   bound="latency"),
                     gflops=5.0 * N * 16 / (us * 1e-6) / 1e9, accuracy=acc,
-                    e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=16), gpu_launches=2 * K, clocks=clocks)
+                    e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=16),
+                    gpu_launches=(1 if fused else 2) * K, clocks=clocks)
     elif wl == "B128":
         N1, N2 = 1 << 13, 1 << 14
         N = N1 * N2
@@ -516,7 +535,7 @@ def run_other(args, ranks, local):
         s2 = statistics.mean(ev[k][1].elapsed_time(ev[k][2]) for k in range(K))
         flop = 5.0 * N * 27
         ms = mor(tot) / K
-        fp64_peak = 1250.0
+        fp64_peak, fp64_src = fp64_peak_measured(paco, local)
         dom_ms = max(s1, s2)
         ho = torch.empty_like(xh).pin_memory()
         di = torch.empty_like(x)
@@ -544,7 +563,7 @@ def run_other(args, ranks, local):
                     roofline={"bound": "alu", "kernel": hr["kernel"],
                               "achieved": flop / 2 / (dom_ms * 1e-3) / 1e12, "peak": fp64_peak / 1e3,
                               "unit": "TFLOP/s (nominal 5N log2 N flops, half per stage)",
-                              "peak_source": "nominal FP64 rate of GB300 (1.25 TFLOP/s)",
+                              "peak_source": fp64_src,
                               "frac": flop / 2 / (dom_ms * 1e-3) / 1e12 / (fp64_peak / 1e3),
                               "traffic": None, "hbm": hr},
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, "c128"), gpu_launches=2 * K, clocks=clocks)

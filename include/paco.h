@@ -105,6 +105,8 @@ typedef struct {
     int stage_cluster[2];        /* cluster size used by stage 1 / stage 2 */
     int stage_threads[2];        /* threads per CTA */
     int stage_smem[2];           /* dynamic shared memory per CTA, bytes */
+    int fused_cluster;           /* 1: paco_execute runs the whole transform as one
+                                    cluster launch (see paco_execute) */
 } paco_plan_info_t;
 
 /*
@@ -140,7 +142,20 @@ paco_status_t paco_plan_info(const paco_plan_t *plan, paco_plan_info_t *info);
  * buffers of batch*N elements of the plan's dtype; `out` also holds the
  * intermediate W = Z-hat (Eq. (17)) between the two kernels, so no scratch
  * is used.  in == out, or overlapping buffers, return PACO_ERR_ALIASING.
- * batch = 0 is a no-op.  Asynchronous on `stream`.  Executions of one plan
+ * batch = 0 is a no-op.  Asynchronous on `stream`.  A complex64 plan with
+ * N1 = N2 = 256, p = 4 or 8 and batch <= 16 (where one launch is faster than
+ * two) runs as ONE launch (paco_plan_info.fused_cluster): a thread-block
+ * cluster of K = 16 CTAs per transform (8 where the GPU cannot host a
+ * 16-CTA cluster), processor q of Sect. 2 being the K/p CTAs that hold its
+ * slab -- Phase I on the input columns in shared memory, then PARA-CO-DRP_b
+ * (Sect. 4.2, App. C.5) as one all-to-all of asynchronous stores into the
+ * other CTAs' shared memory (N/p^2 items per ordered pair of processors, a
+ * CTA's items for itself kept in the CTA), then Phase
+ * III on its output columns; W never reaches global memory.  The launch
+ * allows programmatic dependent launch (it waits for the preceding kernels
+ * before it reads `in`).  A device-side wait of this form that gives up after
+ * 2 s sets the status word that paco_plan_check reads (PACO_ERR_TIMEOUT).
+ * Executions of one plan
  * must not overlap in time (a plan with a 2^14 complex64 factor, and an
  * uneven-batch plan, run pipelines whose ring buffers and counters the plan
  * owns): use one plan per concurrently used stream.
@@ -271,10 +286,27 @@ paco_status_t paco_plan_batched_config(const paco_plan_t *plan, int64_t length, 
  * replaces the default poll limit (0 restores it); wait_bias is added to every
  * counter target, so with wait_bias > 0 no such wait can be met: the next
  * execution of the plan returns garbage and paco_plan_check reports
- * PACO_ERR_TIMEOUT, and the CUDA context stays usable.  Set both to 0 for
- * normal use.  Returns PACO_ERR_INVALID_ARG for a NULL plan.
+ * PACO_ERR_TIMEOUT, and the CUDA context stays usable.  In the one-launch
+ * cluster form (fused_cluster = 1) wait_bias > 0 makes each CTA's transaction
+ * barrier expect 8 * wait_bias bytes that never come, so its 2 s wait runs
+ * out the same way.  Set both to 0 for normal use.  Returns
+ * PACO_ERR_INVALID_ARG for a NULL plan.
  */
 paco_status_t paco_debug_set_waits(paco_plan_t *plan, unsigned spin_limit, unsigned wait_bias);
+
+/*
+ * paco_debug_exchange_counts -- test hook (the paper has no counterpart):
+ * runs paco_execute of a one-launch cluster plan (fused_cluster = 1) once,
+ * counting the items each CTA writes to each destination CTA in the
+ * all-to-all, added up per ordered pair of processors, and stores them in
+ * counts[q * p + q'] (p x p, source processor q, destination q'), for every
+ * transform of the batch added together; waits
+ * for the result.  Theorem 4 fixes each count at batch * N/p^2.  Allocates a
+ * small device buffer (a test hook, not an execution entry point).
+ * PACO_ERR_UNSUPPORTED for other plans.
+ */
+paco_status_t paco_debug_exchange_counts(paco_plan_t *plan, const void *in, void *out, int dir,
+                                         int64_t *counts, paco_stream_t stream);
 
 /*
  * paco_debug_batched_schedule -- test hook (host only, no GPU): the work
@@ -289,6 +321,19 @@ paco_status_t paco_debug_set_waits(paco_plan_t *plan, unsigned spin_limit, unsig
 int64_t paco_debug_batched_schedule(const int64_t *lengths, int64_t count, int64_t lag_items,
                                     int32_t *kind, int32_t *index, int32_t *tile, int64_t cap,
                                     int32_t *group, int64_t group_cap);
+
+/*
+ * paco_probe_fp64_peak -- measure the FP64 fused multiply-add rate of the
+ * current device (the paper has no counterpart: it is the denominator of the
+ * complex128 roofline, since those transforms are bound by FP64 arithmetic
+ * on this GPU).  One launch of 8 blocks per SM x 256 threads, each running 8
+ * independent chains of 16 * iters FMAs, timed with CUDA events on `stream`
+ * after a short warm-up launch; synchronises the stream.  *gflops receives
+ * the rate (an FMA counts as two flops) at whatever clock the GPU ran, *ms
+ * (may be NULL) the kernel time.  PACO_ERR_INVALID_ARG for iters < 1 or a
+ * NULL gflops.  Allocates nothing.
+ */
+paco_status_t paco_probe_fp64_peak(int64_t iters, double *gflops, float *ms, paco_stream_t stream);
 
 /* Largest batch that paco_execute_noalloc accepts. */
 #define PACO_NOALLOC_MAX_BATCH 16

@@ -74,6 +74,7 @@ class PlanInfo(ctypes.Structure):
         ("h", ctypes.c_int64), ("mu", ctypes.c_int64),
         ("stage_tile_w", ctypes.c_int * 2), ("stage_cluster", ctypes.c_int * 2),
         ("stage_threads", ctypes.c_int * 2), ("stage_smem", ctypes.c_int * 2),
+        ("fused_cluster", ctypes.c_int),
     ]
 
 
@@ -120,10 +121,14 @@ def _load():
     pi = ctypes.POINTER(i32)
     L.paco_plan_batched_config.argtypes = [vp, i64, pi, pi, pi, pi]
     L.paco_plan_batched_config.restype = i32
+    L.paco_debug_exchange_counts.argtypes = [vp, vp, vp, i32, ctypes.POINTER(i64), vp]
+    L.paco_debug_exchange_counts.restype = i32
     L.paco_debug_set_waits.argtypes = [vp, ctypes.c_uint, ctypes.c_uint]
     L.paco_debug_set_waits.restype = i32
     L.paco_execute_noalloc.argtypes = [vp, vp, i32, i64, i32, vp]
     L.paco_execute_noalloc.restype = i32
+    L.paco_probe_fp64_peak.argtypes = [i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), vp]
+    L.paco_probe_fp64_peak.restype = i32
     L.paco_noalloc_check.argtypes = []
     L.paco_noalloc_check.restype = i32
     L.paco_debug_noalloc_set_waits.argtypes = [ctypes.c_uint, ctypes.c_uint]
@@ -143,6 +148,14 @@ def execute_noalloc(x, out, b: int, batch: int, dir: int = -1, stream=None) -> N
     """paco_execute_noalloc: the N1 = N2 = 2^14 complex64 transform without
     any allocation (the library's reserved device arrays); see paco.h."""
     _check(lib.paco_execute_noalloc(_ptr(x), _ptr(out), int(b), int(batch), int(dir), _stream(stream)))
+
+
+def probe_fp64_peak(iters: int = 4096, stream=None):
+    """paco_probe_fp64_peak: (GFLOP/s, ms) of the FP64 FMA rate on the current
+    device (FMA = two flops), at the clock the GPU ran."""
+    g, t = ctypes.c_double(), ctypes.c_float()
+    _check(lib.paco_probe_fp64_peak(int(iters), ctypes.byref(g), ctypes.byref(t), _stream(stream)))
+    return g.value, t.value
 
 
 def noalloc_check() -> None:
@@ -237,6 +250,14 @@ class Plan:
 
     def check(self) -> None:
         _check(lib.paco_plan_check(self._h))
+
+    def debug_exchange_counts(self, x, out, dir: int = -1, stream=None):
+        """Test hook: run a one-launch cluster plan once and return the p x p
+        counts of items each CTA (processor) wrote to each other CTA."""
+        p = int(self.p)
+        arr = (ctypes.c_int64 * (p * p))()
+        _check(lib.paco_debug_exchange_counts(self._h, _ptr(x), _ptr(out), int(dir), arr, _stream(stream)))
+        return [[int(arr[q * p + r]) for r in range(p)] for q in range(p)]
 
     def debug_set_waits(self, spin_limit: int = 0, wait_bias: int = 0) -> None:
         """Test hook of the bounded waits (``paco_debug_set_waits``)."""

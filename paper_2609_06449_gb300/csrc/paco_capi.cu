@@ -266,6 +266,13 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
         return st;
     }
     cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
+    if (cluster_eligible(pl)) {
+        if ((st = cluster_setup(pl)) != PACO_OK) {
+            paco_plan_destroy(pl);
+            return st;
+        }
+        pl->fused = 1;
+    }
     size_t scratch_elems = 0, words = 0;
     for (int k = 0; k < 2; ++k) {
         const StageCfg &sc = pl->st[k];
@@ -320,6 +327,7 @@ extern "C" void paco_plan_destroy(paco_plan_t *pl)
     cudaFree(pl->twL2);
     cudaFree(pl->twN_lo);
     cudaFree(pl->twN_hi);
+    cudaFree(pl->twN_full);
     cudaFree(pl->d_status);
     cudaFree(pl->scratch);
     cudaFree(pl->ctr);
@@ -343,6 +351,7 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
     info->items_per_pair = pl->N / (p * p);
     info->h = pl->N / p - pl->N / (p * p);
     info->mu = pl->N - pl->N / p;
+    info->fused_cluster = pl->fused;
     for (int s = 0; s < 2; ++s) {
         info->stage_tile_w[s] = 1 << pl->st[s].lgW;
         info->stage_cluster[s] = 1 << pl->st[s].lgK;
@@ -484,6 +493,7 @@ extern "C" paco_status_t paco_execute(paco_plan_t *pl, const void *in, void *out
     set_device(pl);
     cudaStream_t s = (cudaStream_t)stream;
     if (pl->bs) return batched_execute(pl, in, out, dir, s);
+    if (pl->fused) return launch_cluster(pl, in, out, dir, nullptr, s);
     if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s)) != PACO_OK) return st;
     return launch_stage(pl, pl->st[1], 2, out, out, dir, s);
 }
@@ -553,6 +563,30 @@ extern "C" paco_status_t paco_plan_check(paco_plan_t *pl)
     PACO_CUDA_TRY(cudaMemset(pl->d_status, 0, sizeof(int)));
     if (h == PACO_ERR_TIMEOUT) return fail(PACO_ERR_TIMEOUT, "a bounded device wait gave up");
     if (h != 0) return fail(PACO_ERR_DEVICE, "device status word %d", h);
+    return PACO_OK;
+}
+
+extern "C" paco_status_t paco_debug_exchange_counts(paco_plan_t *pl, const void *in, void *out, int dir,
+                                                   int64_t *counts, paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, in, out, dir, false);
+    if (st != PACO_OK) return st;
+    if (!pl->fused) return fail(PACO_ERR_UNSUPPORTED, "paco_debug_exchange_counts: the plan is not a one-launch cluster plan");
+    if (!counts) return fail(PACO_ERR_INVALID_ARG, "counts is NULL");
+    set_device(pl);
+    const int p = pl->p;
+    unsigned *d = nullptr;
+    PACO_CUDA_TRY(cudaMalloc(&d, sizeof(unsigned) * p * p));
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned) * p * p, s);
+    if (e == cudaSuccess && pl->batch > 0) st = launch_cluster(pl, in, out, dir, d, s);
+    unsigned h[256] = {0};
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(unsigned) * p * p, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(PACO_ERR_CUDA, "paco_debug_exchange_counts: %s", cudaGetErrorString(e));
+    if (st != PACO_OK) return st;
+    for (int k = 0; k < p * p; ++k) counts[k] = (int64_t)h[k];
     return PACO_OK;
 }
 

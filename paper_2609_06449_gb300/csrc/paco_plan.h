@@ -46,6 +46,8 @@ struct paco_plan {
     unsigned dbg_spin_limit = 0;   // paco_debug_set_waits: poll limit of the bounded waits (0 = default)
     unsigned dbg_wait_bias = 0;    // paco_debug_set_waits: added to the dependency targets
     void *tc = nullptr;            // its fragment table
+    int fused = 0;                 // 1: paco_execute is one cluster launch (paco_cluster.cu)
+    void *twN_full = nullptr;      // one-launch form: w_N^{-r}, r < N
     // uneven batch (paco_plan_create_batched): N = total elements, batch = 1
     paco::BatchedState *bs = nullptr;
 };
@@ -64,6 +66,12 @@ paco_status_t tc_table_create(int form, void **out);
 
 // paco_permute.cu
 paco_status_t launch_permute(const paco_plan *pl, const void *A_tilde, void *W, int dir,
+                             cudaStream_t stream);
+
+// paco_cluster.cu
+bool cluster_eligible(const paco_plan *pl);
+paco_status_t cluster_setup(paco_plan *pl);
+paco_status_t launch_cluster(const paco_plan *pl, const void *in, void *out, int dir, unsigned *pair_count,
                              cudaStream_t stream);
 
 // paco_batched.cu

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paco_inputs import gaussian
+from paco_inputs import gaussian, uniform
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -73,3 +73,22 @@ def test_batched_phase3_wait_gives_up_and_context_survives():
     for n in lengths:
         assert _rel(y[off:off + n].reshape(1, -1), x[off:off + n].reshape(1, -1)) <= 5e-7 * math.log2(n)
         off += n
+
+
+def test_one_launch_cluster_wait_gives_up_and_context_survives():
+    """The one-launch form's transaction barrier made to expect bytes that no
+    CTA sends: every CTA's 2 s wait gives up, the status word reads
+    PACO_ERR_TIMEOUT, and the next transform is correct."""
+    N = 65536
+    plan = paco.Plan(256, 256, 2, 1, paco.C64, p=4)
+    assert plan.info.fused_cluster == 1
+    x = np.asarray(uniform(N, 95, np.complex64)).reshape(1, N)
+    xt = torch.from_numpy(x).cuda()
+    out = torch.empty_like(xt)
+
+    def run():
+        plan.execute(xt, out, -1)
+        return out.cpu().numpy()
+
+    y = _expect_timeout_then_recover(plan, x, run)
+    assert _rel(y, x) <= 5e-7 * 16

@@ -471,3 +471,114 @@ def test_panel_shared_accesses_are_conflict_free():
             for k8 in range(8):
                 assert conflict_free(lanes(lambda q, col, cc, half, box:
                                            box + (q << 7) + ((cc ^ q) << 4) + h * 1024 + k8 * 2048))
+
+
+# ---------------------------------------------------------------------------
+# The one-launch cluster form (paco_cluster.cu): N1 = N2 = 256, p = 4 or 8
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("K,p,b", [(16, 4, 2), (16, 8, 2), (16, 4, 4), (8, 4, 2), (8, 8, 2)])
+@pytest.mark.parametrize("conj", [False, True])
+def test_cluster_kernel_model(K, p, b, conj):
+    """Every CTA of a K-CTA cluster with the kernel's index formulas (CTA r
+    owns 256/K input and output columns; processor q is CTAs q K/p ..):
+    Phase I through the radix 16 x 16 exchange (pass 2 in the t16-fast role),
+    the all-to-all into the destination CTAs' swizzled W parts (each slot
+    written exactly once, in bounds -- the bytes each CTA's transaction
+    barrier expects; N/K^2 items per ordered pair of CTAs and N/p^2 per
+    ordered pair of processors), Phase III over the digit-reversed rows, and
+    the output positions -- equal to the DFT.  Every shared-memory access
+    pattern is checked for half-warp bank conflicts."""
+    import oracle
+    L, N = 256, 65536
+    t = {2: 1, 4: 2, 16: 4}[b]
+    pi = oracle.digit_reverse_table(b, 8 // t)
+    W1 = W2 = L // K
+    nt = N // K // 16
+    rng = np.random.default_rng(K + p + b)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    w256 = np.exp(-2j * np.pi * np.arange(256) / 256)
+    wN = lambda r: np.exp(-2j * np.pi * (r % N) / N)
+    sw = lambda row: row >> 4
+
+    def banks_ok(addrs):
+        """16 lanes of a half-warp, 8-byte words: 16 different banks."""
+        return len({a_ % 16 for a_ in addrs}) == 16
+
+    def dft256_cols(vals, W, t16_fast):
+        """vals[tid] = the 16 pass-1 inputs of thread tid (col = tid % W,
+        t16 = tid // W); returns (outs, roles): outs[tid] = outputs u + 16 k
+        of column col2, roles[tid] = (col2, u)."""
+        buf = np.full(256 * W, np.nan, complex)
+        for tid in range(nt):
+            col, t16 = tid % W, tid // W
+            v = np.fft.fft(vals[tid]) * w256[(np.arange(16) * t16) % 256]
+            for s in range(16):
+                i = (s * 16 + t16) * W + (col ^ s)
+                assert np.isnan(buf[i])
+                buf[i] = v[s]
+        role = (lambda tid: (tid // 16, tid % 16)) if t16_fast else (lambda tid: (tid % W, tid // W))
+        for hw in range(0, nt, 16):
+            for s in range(16):
+                assert banks_ok([(s * 16 + tid // W) * W + ((tid % W) ^ s) for tid in range(hw, hw + 16)])
+            for tt in range(16):
+                assert banks_ok([(role(tid)[1] * 16 + tt) * W + (role(tid)[0] ^ role(tid)[1])
+                                 for tid in range(hw, hw + 16)])
+        outs = []
+        for tid in range(nt):
+            col2, u = role(tid)
+            outs.append(np.fft.fft(np.array([buf[(u * 16 + tt) * W + (col2 ^ u)] for tt in range(16)])))
+        return outs, [role(tid) for tid in range(nt)]
+
+    xin = np.conj(x) if conj else x
+    X = xin.reshape(L, L)
+    parts = [np.full(N // K, np.nan, complex) for _ in range(K)]
+    sent = np.zeros((K, K), int)
+    for r in range(K):
+        vals = [np.array([X[(tid // W1) + 16 * s, r * W1 + tid % W1] for s in range(16)]) for tid in range(nt)]
+        outs, roles = dft256_cols(vals, W1, True)
+        for k in range(16):                                   # exchange stores, per half-warp
+            for hw in range(0, nt, 16):
+                addrs = []
+                for tid in range(hw, hw + 16):
+                    colB, tB = roles[tid]
+                    row = int(pi[r * W1 + colB])
+                    vf = tB + 16 * k
+                    addrs.append(row * W2 + ((vf % W2) ^ sw(row)))
+                assert banks_ok(addrs)
+        for tid in range(nt):
+            colB, tB = roles[tid]
+            c = r * W1 + colB
+            row = int(pi[c])
+            for k in range(16):
+                vf = tB + 16 * k
+                z = outs[tid][k] * wN(vf * c)
+                rd, vl = vf // W2, vf % W2
+                idx = row * W2 + (vl ^ sw(row))
+                assert 0 <= idx < N // K and np.isnan(parts[rd][idx])
+                parts[rd][idx] = z
+                sent[r, rd] += 1
+    assert np.all(sent == N // (K * K))
+    g = K // p
+    per_proc = sent.reshape(p, g, p, g).sum(axis=(1, 3))
+    assert np.all(per_proc == N // (p * p))
+    y = np.full(N, np.nan, complex)
+    for r in range(K):
+        assert not np.isnan(parts[r]).any()                   # every byte the barrier expects landed
+        for hw in range(0, nt, 16):
+            for s_ in range(16):
+                assert banks_ok([int(pi[tid // W2 + 16 * s_]) * W2 + ((tid % W2) ^ sw(int(pi[tid // W2 + 16 * s_])))
+                                 for tid in range(hw, hw + 16)])
+        vals = []
+        for tid in range(nt):
+            vl, u16 = tid % W2, tid // W2
+            rows = [int(pi[u16 + 16 * s]) for s in range(16)]
+            vals.append(np.array([parts[r][rr * W2 + (vl ^ sw(rr))] for rr in rows]))
+        outs, roles = dft256_cols(vals, W2, False)
+        for tid in range(nt):
+            vl, u16 = roles[tid]
+            for k in range(16):
+                k2 = u16 + 16 * k
+                y[k2 * L + r * W2 + vl] = np.conj(outs[tid][k]) if conj else outs[tid][k]
+    want = np.fft.fft(x) if not conj else np.fft.ifft(x) * N
+    assert np.allclose(y, want, atol=1e-8 * np.sqrt(N))

@@ -114,6 +114,45 @@ def test_config_a_and_direct_dft_subcase():
     assert rel_l2(got10, ref10.reshape(1, -1)) <= 5e-7 * 10
 
 
+@pytest.mark.parametrize("b,p", [(2, 4), (2, 8), (4, 4)])
+def test_one_launch_cluster_form(b, p):
+    """N1 = N2 = 256 with p = 4 or 8 runs as one cluster launch (CTA q =
+    processor q): against the oracle in both directions with a ragged batch
+    of 3, against the two-launch path (stage 1 + stage 2 through W in global
+    memory), and the all-to-all's item counts per ordered pair, measured in
+    the kernel, equal to batch * N/p^2 (Theorem 4)."""
+    N1 = N2 = 256
+    N, batch = N1 * N2, 3
+    plan = paco.Plan(N1, N2, b, batch, paco.C64, p=p)
+    assert plan.info.fused_cluster == 1
+    x = uniform(batch * N, 70 + p + b, np.complex64).reshape(batch, N)
+    xt = torch.from_numpy(x).cuda()
+    for d in (-1, 1):
+        got = run(plan, x, d)
+        ref = oracle.fft(x.astype(np.complex128), dir=d)
+        assert rel_l2(got, ref) <= 5e-7 * 16, d
+        two = torch.empty_like(xt)
+        plan.execute_stage1(xt, two, d)
+        plan.execute_stage2(two, two, d)
+        torch.cuda.synchronize()
+        assert rel_l2(got, two.cpu().numpy().astype(np.complex128)) <= 5e-7 * 16
+    out = torch.empty_like(xt)
+    counts = plan.debug_exchange_counts(xt, out)
+    assert counts == [[batch * N // (p * p)] * p for _ in range(p)]
+    assert rel_l2(out.cpu().numpy(), oracle.fft(x.astype(np.complex128))) <= 5e-7 * 16
+
+
+def test_one_launch_form_batch_limit():
+    """The one-launch form takes up to 16 transforms; 17 run as two stage
+    launches.  Both against the oracle."""
+    N = 65536
+    for batch, fused in ((16, 1), (17, 0)):
+        plan = paco.Plan(256, 256, 2, batch, paco.C64, p=4)
+        assert plan.info.fused_cluster == fused
+        x = uniform(batch * N, 90 + batch, np.complex64).reshape(batch, N)
+        assert rel_l2(run(plan, x), oracle.fft(x.astype(np.complex128))) <= 5e-7 * 16
+
+
 def test_closed_forms_on_gpu():
     """delta -> constant; single tone -> N delta; Parseval."""
     N1 = N2 = 256
