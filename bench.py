@@ -714,11 +714,19 @@ def run_other(args, ranks, local):
         w = wh.cuda()
 
         def loss_of(yv):
-            # sum(w |y|^2) on the (re, im) view: no copies of the complex parts
+            # sum(w |y|^2) on the (re, im) view: the unfused composition, for context
             yr = torch.view_as_real(yv)
             return (w * (yr * yr).sum(-1)).sum()
 
         def step():
+            # the loss summed in the Phase III kernel, its backward fused into
+            # the conjugate transform's loads
+            x.grad = None
+            loss = paco.weighted_power_loss(x, w, N1, N2, 4)
+            loss.backward()
+            return loss
+
+        def step_unfused():
             x.grad = None
             loss = loss_of(paco.PacoFFT.apply(x, N1, N2, 4))
             loss.backward()
@@ -726,6 +734,7 @@ def run_other(args, ranks, local):
         for _ in range(W):
             step()
         tot, per, clocks = timed(step)
+        tot_u, _ = time_steps(step_unfused, min(K, 20), 3, stream)
         flop = 2 * 5.0 * N * 20 * B
         import oracle
         step()
@@ -742,7 +751,7 @@ def run_other(args, ranks, local):
 
         def step_host():
             xd = xh.to("cuda", non_blocking=True).requires_grad_(True)
-            loss = loss_of(paco.PacoFFT.apply(xd, N1, N2, 4))
+            loss = paco.weighted_power_loss(xd, w, N1, N2, 4)
             loss.backward()
             gh.copy_(xd.grad, non_blocking=True)
         e2e = None if args.no_e2e else e2e_host(step_host, max(args.e2e_steps, 1), stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
@@ -750,10 +759,15 @@ def run_other(args, ranks, local):
         line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s (forward + backward transforms)",
                     higher_is_better=True, ms_per_step=ms, dtype="f32",
                     config={"workload": "256 x c64 1-D DFT N=2^20 (1024 x 1024, b=4): loss = sum(w |FFT(x)|^2), "
-                                        "forward + backward (conjugate transform) through torch.autograd",
+                                        "forward + backward (conjugate transform) through torch.autograd, "
+                                        "the loss and its backward fused into the stage kernels",
                             "input": "x Re, Im i.i.d. N(0,1); w U[0,1)", "l2": "inputs larger than L2"},
-                    accuracy=acc, context=cufft_context(x.detach(), N, B, flop / 2),
-                    roofline=hbm_roofline("stage kernels (4 launches + torch loss ops)", 4 * 16.0 * N * B, ms),
+                    accuracy=acc,
+                    context=dict(cufft_context(x.detach(), N, B, flop / 2),
+                                 unfused_ms_per_step=mor(tot_u) / min(K, 20),
+                                 unfused="PacoFFT + the loss and its gradient as PyTorch element-wise ops"),
+                    roofline=hbm_roofline("stage kernels (4 launches; w read by the loss epilogue and the "
+                                          "backward's loads)", (4 * 16.0 + 2 * 4.0) * N * B, ms),
                     e2e=e2e, cpu_baseline=cpu_leg(args, rank, world, lg=20), gpu_launches=4 * K, clocks=clocks)
     if rank == 0:
         emit(line)

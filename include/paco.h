@@ -164,6 +164,35 @@ paco_status_t paco_execute(paco_plan_t *plan, const void *in, void *out, int dir
                            paco_stream_t stream);
 
 /*
+ * paco_execute_weighted_power -- paco_execute plus the weighted power of the
+ * result, for a spectral loss: out = y = F^dir x as paco_execute computes it,
+ * and *loss = sum over the whole batch of w[n] |y[n]|^2, accumulated by the
+ * Phase III kernel as it stores y (the sum is not a separate pass; *loss is
+ * set to 0 on `stream` first, then added to atomically in FP64: its rounding
+ * order varies between runs).  w: device, batch*N floats in the layout of y;
+ * loss: device, one double, 8-byte aligned.  The paper's transform is
+ * unchanged (Theorem 3); the loss is an epilogue of the last stage.  Plans
+ * with a 2^14 complex64 factor (panel stages) and uneven-batch plans return
+ * PACO_ERR_UNSUPPORTED; a one-launch cluster plan runs its two stage launches
+ * here.  Asynchronous on `stream`.
+ */
+paco_status_t paco_execute_weighted_power(paco_plan_t *plan, const void *in, void *out, const float *w,
+                                          double *loss, int dir, paco_stream_t stream);
+
+/*
+ * paco_execute_weighted_input -- out = F^dir (s * w ⊙ in) with the
+ * element-wise product applied as Phase I loads its input (no separate
+ * pass): s = mult * (*scale), or mult when scale is NULL.  w: device,
+ * batch*N floats in the layout of `in`; scale: device double or NULL.  With
+ * dir = +1, w the loss weights, in = y, mult = 2 and scale the incoming
+ * gradient of the loss of paco_execute_weighted_power, out is that loss's
+ * gradient with respect to x (F^H (2 g w ⊙ F x), the conjugate transform
+ * being F^H).  Same plans and errors as paco_execute_weighted_power.
+ */
+paco_status_t paco_execute_weighted_input(paco_plan_t *plan, const void *in, void *out, const float *w,
+                                          const double *scale, float mult, int dir, paco_stream_t stream);
+
+/*
  * paco_execute_stage1 -- Phase I and the fused middle stage only: writes
  * W[u][v] = Z-hat[u, v] = Z[v, pi_m2(u)] with Z[v, c] = A[v, c] w_N^{dir*vc}
  * and A the length-N1 column DFTs (Sect. 4.2, local pack and Eq. (17)),

@@ -12,6 +12,9 @@ Entry points (same names as the C ABI):
 * ``fft(x, N1, N2, b, p=0, dir=-1)`` -- torch tensors on the GPU.
 * ``PacoFFT`` -- ``torch.autograd.Function`` whose backward is the conjugate
   transform (``dir=+1``).
+* ``weighted_power_loss(x, w, N1, N2, b)`` -- sum(w |F x|^2) with the loss
+  summed in the Phase III kernel and its backward fused into the conjugate
+  transform's loads (``paco_execute_weighted_power`` / ``_input``).
 """
 
 from __future__ import annotations
@@ -27,6 +30,8 @@ __all__ = [
     "library_path",
     "fft",
     "PacoFFT",
+    "PacoWeightedPowerLoss",
+    "weighted_power_loss",
     "digit_reverse",
     "C64",
     "C128",
@@ -129,6 +134,10 @@ def _load():
     L.paco_execute_noalloc.restype = i32
     L.paco_probe_fp64_peak.argtypes = [i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), vp]
     L.paco_probe_fp64_peak.restype = i32
+    L.paco_execute_weighted_power.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+    L.paco_execute_weighted_power.restype = i32
+    L.paco_execute_weighted_input.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, i32, vp]
+    L.paco_execute_weighted_input.restype = i32
     L.paco_noalloc_check.argtypes = []
     L.paco_noalloc_check.restype = i32
     L.paco_debug_noalloc_set_waits.argtypes = [ctypes.c_uint, ctypes.c_uint]
@@ -231,6 +240,17 @@ class Plan:
 
     def execute(self, x, out, dir: int = -1, stream=None) -> None:
         _check(lib.paco_execute(self._h, _ptr(x), _ptr(out), int(dir), _stream(stream)))
+
+    def execute_weighted_power(self, x, out, w, loss, dir: int = -1, stream=None) -> None:
+        """out = F^dir x and loss[0] = sum(w |out|^2) (float32 w, float64 loss, device)."""
+        _check(lib.paco_execute_weighted_power(self._h, _ptr(x), _ptr(out), _ptr(w), _ptr(loss), int(dir),
+                                               _stream(stream)))
+
+    def execute_weighted_input(self, x, out, w, scale=None, mult: float = 1.0, dir: int = -1,
+                               stream=None) -> None:
+        """out = F^dir (mult * scale[0] * w * x); scale a float64 device scalar or None."""
+        _check(lib.paco_execute_weighted_input(self._h, _ptr(x), _ptr(out), _ptr(w), _ptr(scale),
+                                               float(mult), int(dir), _stream(stream)))
 
     def execute_stage1(self, x, W, dir: int = -1, stream=None) -> None:
         _check(lib.paco_execute_stage1(self._h, _ptr(x), _ptr(W), int(dir), _stream(stream)))
@@ -371,5 +391,47 @@ try:
         def backward(ctx, g):
             N1, N2, b, p = ctx.cfg
             return fft(g.contiguous(), N1, N2, b, p, dir=+1), None, None, None, None
+    class PacoWeightedPowerLoss(_torch.autograd.Function):
+        """loss = sum(w |F x|^2) over the whole batch (float64 scalar), F the
+        paper's forward transform.  Forward: the two stage kernels, the loss
+        summed by the Phase III kernel as it stores y = F x.  Backward:
+        grad_x = F^H (2 g w ⊙ y), the product applied as the conjugate
+        transform's Phase I loads its input.  w (float32, the shape of x) is
+        treated as a constant."""
+
+        @staticmethod
+        def forward(ctx, x, w, N1, N2, b, p=0):
+            if w.requires_grad:
+                raise ValueError("weighted_power_loss: w is a constant (requires_grad must be False)")
+            xc, wc = x.contiguous(), w.contiguous()
+            N = int(N1) * int(N2)
+            if xc.dtype != _torch.complex64 or wc.dtype != _torch.float32 or wc.shape != xc.shape:
+                raise ValueError("weighted_power_loss: x complex64 and w float32 of the same shape")
+            y = _torch.empty_like(xc)
+            loss = _torch.empty((), dtype=_torch.float64, device=xc.device)
+            stream = int(_torch.cuda.current_stream(xc.device).cuda_stream)
+            with _torch.cuda.device(xc.device.index):
+                pl = get_plan(int(N1), int(N2), int(b), xc.numel() // N, C64, int(p), xc.device.index, stream)
+                pl.execute_weighted_power(xc, y, wc, loss, -1, stream)
+            ctx.save_for_backward(y, wc)
+            ctx.cfg = (int(N1), int(N2), int(b), int(p), stream)
+            return loss
+
+        @staticmethod
+        def backward(ctx, g):
+            y, wc = ctx.saved_tensors
+            N1, N2, b, p, _ = ctx.cfg
+            g = g.to(_torch.float64).contiguous()
+            gx = _torch.empty_like(y)
+            stream = int(_torch.cuda.current_stream(y.device).cuda_stream)
+            with _torch.cuda.device(y.device.index):
+                pl = get_plan(N1, N2, b, y.numel() // (N1 * N2), C64, p, y.device.index, stream)
+                pl.execute_weighted_input(y, gx, wc, g, 2.0, +1, stream)
+            return gx, None, None, None, None, None
+
+    def weighted_power_loss(x, w, N1: int, N2: int, b: int, p: int = 0):
+        """sum(w |F x|^2) (float64 scalar) with the fused forward and backward
+        of ``PacoWeightedPowerLoss``."""
+        return PacoWeightedPowerLoss.apply(x, w, N1, N2, b, p)
 except ImportError:  # pragma: no cover - torch is a hard requirement on the GPU box
-    PacoFFT = None
+    PacoFFT = PacoWeightedPowerLoss = weighted_power_loss = None

@@ -27,6 +27,7 @@ const void *stage_kernel_fn_f32(int lgL, int minb);
 const void *stage_kernel_fn_f64(int lgL, int minb);
 const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
+const void *stage_kernel_fn_terms_f32(int lgL, int minb);
 } // namespace paco
 
 using namespace paco;
@@ -194,6 +195,14 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
     if (two) sc->fn = stage_kernel_fn_f32(lgL, 2);
     PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        227 * 1024));
+    if (!pl->form && pl->esize == 8 && B > 1) {
+        // the weighted-loss variant of the generic kernel (runtime tile width and
+        // cluster size, so it also stands in for a specialised kernel)
+        sc->fn_terms = stage_kernel_fn_terms_f32(lgL, (two || !generic) ? 2 : 1);
+        if (sc->fn_terms)
+            PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn_terms, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               227 * 1024));
+    }
     return PACO_OK;
 }
 
@@ -402,9 +411,15 @@ static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int m
 }
 
 static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int mode,
-                                  const void *in, void *out, int dir, cudaStream_t stream)
+                                  const void *in, void *out, int dir, cudaStream_t stream,
+                                  const StageTerms *terms = nullptr)
 {
-    if (sc.panel) return launch_panel(pl, sc, mode, in, out, dir, stream);
+    if (sc.panel) {
+        if (terms) return fail(PACO_ERR_UNSUPPORTED, "weighted terms: not in the 2^14 panel stages");
+        return launch_panel(pl, sc, mode, in, out, dir, stream);
+    }
+    if (terms && !sc.fn_terms)
+        return fail(PACO_ERR_UNSUPPORTED, "weighted terms: complex64 plans with both factors >= 4 only");
     StageArgs a;
     memset(&a, 0, sizeof(a));
     a.in = in;
@@ -438,6 +453,13 @@ static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int m
         StageArgs ab = a;
         ab.in = (const char *)in + (size_t)(b0 * pl->N) * pl->esize;
         ab.out = (char *)out + (size_t)(b0 * pl->N) * pl->esize;
+        StageTerms tb;
+        memset(&tb, 0, sizeof(tb));
+        if (terms) {
+            tb = *terms;
+            if (tb.ld_w) tb.ld_w += b0 * pl->N;
+            if (tb.st_w) tb.st_w += b0 * pl->N;
+        }
         cudaLaunchConfig_t cfg;
         memset(&cfg, 0, sizeof(cfg));
         cfg.gridDim = dim3((unsigned)(sc.ntiles * K), (unsigned)nb, 1);
@@ -451,8 +473,8 @@ static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int m
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        void *params[] = {&ab};
-        PACO_CUDA_TRY(cudaLaunchKernelExC(&cfg, sc.fn, params));
+        void *params[] = {&ab, &tb};
+        PACO_CUDA_TRY(cudaLaunchKernelExC(&cfg, terms ? sc.fn_terms : sc.fn, params));
     }
     return PACO_OK;
 }
@@ -495,6 +517,60 @@ extern "C" paco_status_t paco_execute(paco_plan_t *pl, const void *in, void *out
     if (pl->bs) return batched_execute(pl, in, out, dir, s);
     if (pl->fused) return launch_cluster(pl, in, out, dir, nullptr, s);
     if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s)) != PACO_OK) return st;
+    return launch_stage(pl, pl->st[1], 2, out, out, dir, s);
+}
+
+// Plans whose two stages are the generic stage kernels take the weighted terms.
+static paco_status_t check_weighted(const paco_plan *pl, const char *fn)
+{
+    if (pl->bs) return fail(PACO_ERR_UNSUPPORTED, "%s takes a single-length plan", fn);
+    if (pl->st[0].panel || pl->st[1].panel)
+        return fail(PACO_ERR_UNSUPPORTED, "%s: plans with a 2^14 complex64 factor (panel stages) are not supported", fn);
+    if (!pl->st[0].fn_terms || !pl->st[1].fn_terms)
+        return fail(PACO_ERR_UNSUPPORTED, "%s: plain complex64 plans with both factors >= 4 only", fn);
+    return PACO_OK;
+}
+
+extern "C" paco_status_t paco_execute_weighted_power(paco_plan_t *pl, const void *in, void *out, const float *w,
+                                                     double *loss, int dir, paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, in, out, dir, false);
+    if (st != PACO_OK) return st;
+    if ((st = check_weighted(pl, "paco_execute_weighted_power")) != PACO_OK) return st;
+    if (!w || !loss) return fail(PACO_ERR_INVALID_ARG, "paco_execute_weighted_power: w and loss required");
+    if (((uintptr_t)w & 3u) || ((uintptr_t)loss & 7u))
+        return fail(PACO_ERR_INVALID_ARG, "paco_execute_weighted_power: w must be 4-byte, loss 8-byte aligned");
+    set_device(pl);
+    cudaStream_t s = (cudaStream_t)stream;
+    PACO_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(double), s));
+    if (pl->batch == 0) return PACO_OK;
+    StageTerms t;
+    memset(&t, 0, sizeof(t));
+    t.st_w = w;
+    t.st_loss = loss;
+    if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s)) != PACO_OK) return st;
+    return launch_stage(pl, pl->st[1], 2, out, out, dir, s, &t);
+}
+
+extern "C" paco_status_t paco_execute_weighted_input(paco_plan_t *pl, const void *in, void *out, const float *w,
+                                                     const double *scale, float mult, int dir,
+                                                     paco_stream_t stream)
+{
+    paco_status_t st = check_exec(pl, in, out, dir, false);
+    if (st != PACO_OK) return st;
+    if ((st = check_weighted(pl, "paco_execute_weighted_input")) != PACO_OK) return st;
+    if (!w) return fail(PACO_ERR_INVALID_ARG, "paco_execute_weighted_input: w required");
+    if (((uintptr_t)w & 3u) || ((uintptr_t)scale & 7u))
+        return fail(PACO_ERR_INVALID_ARG, "paco_execute_weighted_input: w must be 4-byte, scale 8-byte aligned");
+    if (pl->batch == 0) return PACO_OK;
+    set_device(pl);
+    cudaStream_t s = (cudaStream_t)stream;
+    StageTerms t;
+    memset(&t, 0, sizeof(t));
+    t.ld_w = w;
+    t.ld_scale = scale;
+    t.ld_mult = mult;
+    if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s, &t)) != PACO_OK) return st;
     return launch_stage(pl, pl->st[1], 2, out, out, dir, s);
 }
 

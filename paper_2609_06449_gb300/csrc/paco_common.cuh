@@ -191,4 +191,14 @@ struct StageArgs {
     const void *tc;         // tensor-core forms: fragment table (paco_tc.cuh)
 };
 
+// Element-wise terms of a weighted power loss, taken by the stage kernels
+// built with them (paco_stage_kernel_terms); nullptr switches a term off.
+struct StageTerms {
+    const float *ld_w;      // mode 1: element n of the input is read as
+    const double *ld_scale; //   ld_mult * (*ld_scale or 1) * ld_w[n] * in[n]
+    float ld_mult;
+    const float *st_w;      // mode 2: *st_loss += sum over n of st_w[n] |out[n]|^2
+    double *st_loss;
+};
+
 } // namespace paco

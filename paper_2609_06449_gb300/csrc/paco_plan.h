@@ -18,6 +18,7 @@ struct StageCfg {
     int smem = 0;     // dynamic shared memory, bytes
     int ntiles = 0;   // column tiles per transform
     const void *fn = nullptr;
+    const void *fn_terms = nullptr;   // the same stage with the weighted-loss terms (complex64), or nullptr
     int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
     int P = 0;        // panel width (columns)
 };

@@ -108,9 +108,9 @@ __host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int 
 // FORM != TC_NONE computes the radix-16 passes (F1 and F2 pass 1 when the
 // radix is 16) as tensor-core contractions (paco_tc.cuh); its fragment table
 // and per-warp staging follow the stage's shared memory.
-template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE>
+template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE, bool TERMS = false>
 __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long long boff, int rank,
-                                           unsigned char *smem_raw)
+                                           unsigned char *smem_raw, const StageTerms *terms = nullptr)
 {
     using C = cx<R>;
     constexpr int L = A * B;
@@ -197,6 +197,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
 
     C v[EPT];
     const C *gin = reinterpret_cast<const C *>(args.in) + boff;
+    // weighted input (mode 1): one real factor per element
+    bool ldw = false;
+    R lds = R(1);
+    if constexpr (TERMS) {
+        ldw = (mode == 1) && terms->ld_w != nullptr;
+        if (ldw) lds = R(terms->ld_mult) * (terms->ld_scale ? R(__ldg(terms->ld_scale)) : R(1));
+    }
 
     // ---- F1 pass 1: radix RA1 over j_hi, span RA2; operands straight from HBM
     {
@@ -214,6 +221,11 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                                                  : (unsigned)j;
                 C x = LDCG ? ldcg_cx(gin + (long long)row * args.C + c0 + col)
                            : ldg_cx(gin + (long long)row * args.C + c0 + col);
+                if constexpr (TERMS) if (ldw) {
+                    const R f = lds * R(__ldg(terms->ld_w + boff + (long long)row * args.C + c0 + col));
+                    x.x *= f;
+                    x.y *= f;
+                }
                 x.y *= csign;
                 v[u * RA1 + r] = x;
             }
@@ -382,6 +394,9 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     // ---- F2 pass 2 (if B > 16) and the store
     constexpr int RL = (RB2 > 1) ? RB2 : RB1;    // radix of the last pass
     constexpr int NBL = EPT / RL;
+    bool stw = false;                             // weighted power of the output
+    if constexpr (TERMS) stw = (mode == 2) && terms->st_w != nullptr;
+    R wpow = R(0);
     if constexpr (RB2 > 1) __syncthreads();
 #pragma unroll
     for (int u = 0; u < NBL; ++u) {
@@ -414,6 +429,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
         }
         const int klo = rank * Ak + al;
         const int c = c0 + col;
+        float wv[TERMS ? RL : 1];                     // the loss weights of this thread's outputs, loaded first
+        if constexpr (TERMS) if (stw) {
+#pragma unroll
+            for (int k = 0; k < RL; ++k) {
+                const int khi = (RB2 > 1) ? (hi + RB1 * k) : k;
+                wv[k] = __ldg(terms->st_w + boff + (long long)(klo + A * khi) * args.out_ld + c);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < RL; ++k) {
             const int khi = (RB2 > 1) ? (hi + RB1 * k) : k;
@@ -426,12 +449,31 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                 idx = (long long)urow * args.out_ld + kk;
             } else if (mode == 2) {
                 idx = (long long)kk * args.out_ld + c;
+                if constexpr (TERMS) if (stw) wpow += R(wv[k]) * (y.x * y.x + y.y * y.y);
             } else {
                 const unsigned arow = digit_reverse((unsigned)kk, args.rev_bits, args.rev_t);
                 idx = (long long)arow * args.out_ld + c;
             }
             y.y *= csign;
             st_cx(gout + idx, y);
+        }
+    }
+    if constexpr (TERMS) if (stw) {
+        if (NT & 31) {
+            atomicAdd(terms->st_loss, (double)wpow);         // tiny tiles: one atomic per thread
+        } else {
+            // warp sums in the (now unused) tile buffer, then one FP64 atomic per CTA
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wpow += __shfl_xor_sync(0xffffffffu, wpow, o);
+            double *wsum = reinterpret_cast<double *>(smem_raw);
+            __syncthreads();                                  // every read of the tile is done
+            if ((tid & 31) == 0) wsum[tid >> 5] = (double)wpow;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int i = 0; i < NT / 32; ++i) t += wsum[i];
+                atomicAdd(terms->st_loss, t);
+            }
         }
     }
 }
@@ -445,6 +487,19 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs a
     if ((1 << lgK) > 1) rank = (int)cg::this_cluster().block_rank();
     stage_tile<R, A, B, LGWC, LGKC, MC, false, FORM>(args, (int)(blockIdx.x >> lgK),
                                                      (long long)blockIdx.y * args.batch_stride, rank, smem_raw);
+}
+
+// The generic stage with the element-wise terms of a weighted power loss
+// (StageTerms) compiled in; paco_stage_kernel carries none of their code.
+template <typename R, int A, int B, int MINB>
+__global__ void __launch_bounds__(512, MINB) paco_stage_kernel_terms(const StageArgs args, const StageTerms terms)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int rank = 0;
+    if ((1 << args.lgK) > 1) rank = (int)cg::this_cluster().block_rank();
+    stage_tile<R, A, B, -1, -1, 0, false, TC_NONE, true>(args, (int)(blockIdx.x >> args.lgK),
+                                                         (long long)blockIdx.y * args.batch_stride, rank, smem_raw,
+                                                         &terms);
 }
 
 // L = A (B == 1): the whole transform is F1; store straight from F1's layout.

@@ -7,7 +7,7 @@
 namespace paco {
 
 // lgL -> (A, B) = (2^ceil(lgL/2), 2^floor(lgL/2)), the balanced split.
-template <typename R, int LGL>
+template <typename R, int LGL, bool TERMS>
 struct StageKernel {
     static constexpr int A = 1 << ((LGL + 1) / 2);
     static constexpr int B = 1 << (LGL / 2);
@@ -15,32 +15,37 @@ struct StageKernel {
     // registers at 64 per thread; complex64 only)
     static const void *fn(int minb)
     {
-        if constexpr (B == 1) return reinterpret_cast<const void *>(&paco_stage_kernel_b1<R, A>);
-        else if constexpr (sizeof(R) == 4) {
+        if constexpr (B == 1) return TERMS ? nullptr : reinterpret_cast<const void *>(&paco_stage_kernel_b1<R, A>);
+        else if constexpr (TERMS) {
+            if (minb == 2) return reinterpret_cast<const void *>(&paco_stage_kernel_terms<R, A, B, 2>);
+            return reinterpret_cast<const void *>(&paco_stage_kernel_terms<R, A, B, 1>);
+        } else if constexpr (sizeof(R) == 4) {
             if (minb == 2) return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B, -1, -1, 0, 2>);
             return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B>);
         } else return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B>);
     }
 };
 
-template <typename R>
+// The generic stage kernel for length 2^lgL; TERMS = true: the variant with
+// the weighted-loss terms (StageArgs::ld_w, st_w) compiled in.
+template <typename R, bool TERMS = false>
 const void *stage_kernel_fn(int lgL, int minb)
 {
     switch (lgL) {
-    case 1: return StageKernel<R, 1>::fn(minb);
-    case 2: return StageKernel<R, 2>::fn(minb);
-    case 3: return StageKernel<R, 3>::fn(minb);
-    case 4: return StageKernel<R, 4>::fn(minb);
-    case 5: return StageKernel<R, 5>::fn(minb);
-    case 6: return StageKernel<R, 6>::fn(minb);
-    case 7: return StageKernel<R, 7>::fn(minb);
-    case 8: return StageKernel<R, 8>::fn(minb);
-    case 9: return StageKernel<R, 9>::fn(minb);
-    case 10: return StageKernel<R, 10>::fn(minb);
-    case 11: return StageKernel<R, 11>::fn(minb);
-    case 12: return StageKernel<R, 12>::fn(minb);
-    case 13: return StageKernel<R, 13>::fn(minb);
-    case 14: return StageKernel<R, 14>::fn(minb);
+    case 1: return StageKernel<R, 1, TERMS>::fn(minb);
+    case 2: return StageKernel<R, 2, TERMS>::fn(minb);
+    case 3: return StageKernel<R, 3, TERMS>::fn(minb);
+    case 4: return StageKernel<R, 4, TERMS>::fn(minb);
+    case 5: return StageKernel<R, 5, TERMS>::fn(minb);
+    case 6: return StageKernel<R, 6, TERMS>::fn(minb);
+    case 7: return StageKernel<R, 7, TERMS>::fn(minb);
+    case 8: return StageKernel<R, 8, TERMS>::fn(minb);
+    case 9: return StageKernel<R, 9, TERMS>::fn(minb);
+    case 10: return StageKernel<R, 10, TERMS>::fn(minb);
+    case 11: return StageKernel<R, 11, TERMS>::fn(minb);
+    case 12: return StageKernel<R, 12, TERMS>::fn(minb);
+    case 13: return StageKernel<R, 13, TERMS>::fn(minb);
+    case 14: return StageKernel<R, 14, TERMS>::fn(minb);
     default: return nullptr;
     }
 }

@@ -91,3 +91,58 @@ def test_analytic_adjoint_full_size():
     errs = np.linalg.norm(g.astype(np.complex128) - want, axis=1) / np.linalg.norm(want, axis=1)
     tol = 5e-7 * math.log2(N)
     assert float(errs.max()) <= tol, f"max rel_l2 {errs.max():.3e} over {batch} gradients"
+
+
+@pytest.mark.parametrize("N1,N2,b,batch", [(32, 32, 2, 3), (64, 256, 4, 2), (1024, 1024, 4, 4)])
+def test_fused_weighted_power_loss(N1, N2, b, batch):
+    """weighted_power_loss (the loss summed by the Phase III kernel, the
+    backward's w-product applied by the conjugate transform's loads): the
+    loss against sum(w |F x|^2) from the oracle (relative error <= 1e-6, the
+    FP32 rounding of y), the output y against the oracle's F x, and the
+    gradient with an upstream factor of 3 against 6 F^H (w * F x), every
+    transform element by element within 5e-7 * log2 N."""
+    N = N1 * N2
+    xh = gaussian(batch * N, 11 + b, np.complex64).reshape(batch, N)
+    wh = weights(batch * N, 12 + b).reshape(batch, N)
+    x = torch.from_numpy(xh).cuda().requires_grad_(True)
+    wt = torch.from_numpy(wh).cuda()
+    loss = paco.weighted_power_loss(x, wt, N1, N2, b)
+    assert loss.dtype == torch.float64 and loss.dim() == 0
+    (3.0 * loss).backward()
+    yo = oracle.fft(xh.astype(np.complex128), -1, threads=0)
+    want_loss = float(np.sum(wh.astype(np.float64) * np.abs(yo) ** 2))
+    assert abs(loss.item() - want_loss) <= 1e-6 * want_loss
+    want = 6.0 * oracle.fft(yo * wh.astype(np.float64), +1, threads=0)
+    g = x.grad.cpu().numpy().astype(np.complex128)
+    errs = np.linalg.norm(g - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert float(errs.max()) <= 5e-7 * math.log2(N), errs.max()
+
+
+def test_fused_loss_matches_unfused_path():
+    """The fused loss and gradient equal the unfused composition
+    (PacoFFT + PyTorch's w |y|^2) to FP32 rounding."""
+    N1 = N2 = 64
+    N, batch = N1 * N2, 5
+    xh = gaussian(batch * N, 21, np.complex64).reshape(batch, N)
+    wt = torch.from_numpy(weights(batch * N, 22).reshape(batch, N)).cuda()
+    xa = torch.from_numpy(xh).cuda().requires_grad_(True)
+    xb = torch.from_numpy(xh).cuda().requires_grad_(True)
+    la = paco.weighted_power_loss(xa, wt, N1, N2, 2)
+    la.backward()
+    yb = paco.PacoFFT.apply(xb, N1, N2, 2)
+    lb = (wt * torch.view_as_real(yb).pow(2).sum(-1)).sum()
+    lb.backward()
+    assert abs(la.item() - lb.item()) <= 1e-5 * abs(lb.item())
+    d = (xa.grad - xb.grad).abs().max().item()
+    assert d <= 1e-5 * xb.grad.abs().max().item()
+
+
+def test_fused_loss_rejects_panel_plans():
+    """Plans with a 2^14 complex64 factor (panel stages) do not take the
+    weighted terms: PACO_ERR_UNSUPPORTED, nothing launched."""
+    N1, N2 = 1 << 14, 128
+    x = torch.zeros(N1 * N2, dtype=torch.complex64, device="cuda")
+    w = torch.ones(N1 * N2, dtype=torch.float32, device="cuda")
+    with pytest.raises(paco.PacoError) as e:
+        paco.weighted_power_loss(x, w, N1, N2, 2)
+    assert e.value.status == 2                               # PACO_ERR_UNSUPPORTED
