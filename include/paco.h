@@ -107,6 +107,8 @@ typedef struct {
     int stage_smem[2];           /* dynamic shared memory per CTA, bytes */
     int fused_cluster;           /* 1: paco_execute runs the whole transform as one
                                     cluster launch (see paco_execute) */
+    int shard_G;                 /* sharded plan: G ranks (0: not sharded) */
+    int shard_rank;              /* sharded plan: this rank */
 } paco_plan_info_t;
 
 /*
@@ -162,6 +164,52 @@ paco_status_t paco_plan_info(const paco_plan_t *plan, paco_plan_info_t *info);
  */
 paco_status_t paco_execute(paco_plan_t *plan, const void *in, void *out, int dir,
                            paco_stream_t stream);
+
+/*
+ * The sharded form -- PARA-CO-DRP across G ranks (Sect. 4.2, App. C.5; one
+ * GPU per rank, G = p processors).  Rank g holds input slab g, the columns
+ * c in [g Cl, (g+1) Cl) of X = x viewed N1 x N2 (Cl = N2/G), and gets output
+ * slab g, the columns k1 in [g K1, (g+1) K1) of Y = y viewed N2 x N1
+ * (K1 = N1/G).  Per rank:
+ *   paco_shard_stage1  Phase I on the local slab (length-N1 column DFTs, the
+ *                      top-level twiddle w_N^{-k1 c} at the global column c),
+ *                      stored as G send blocks of N/G^2 items (Theorem 4):
+ *                      block q' holds k1 in rank q''s slab, its rows in the
+ *                      order pi(c - g Cl) -- the digit reversal over the
+ *                      local column's digits, the part of pi_m2 that stays on
+ *                      the rank (Eq. (17) with c = g Cl + c_l: pi_m2(c) =
+ *                      pi(c_l) G + pi(g));
+ *   (exchange)         block q' of every rank's send buffer goes to rank q',
+ *                      into block g of its receive buffer (an all-to-all of
+ *                      equal blocks, e.g. NCCL grouped send/recv or
+ *                      torch.distributed.all_to_all_single; the caller runs
+ *                      it -- this library holds no communicator);
+ *   paco_shard_stage2  Phase III on the local output columns, reading W row
+ *                      pi_m2(j), j = j_h Cl + j_l, as row pi(j_l) of the block
+ *                      from rank j_h.
+ * Layouts (complex64, device): x_local [batch][N1][Cl]; send and recv
+ * [G][batch][Cl][K1] (block for / from rank g, N/G^2 items per transform);
+ * y_local [batch][N2][K1].  G must be a power of b with 2 <= G, G | N1 and
+ * G | N2, N2/G >= b; batch <= 65535.  dir = +1 is the conjugate transform, as in
+ * paco_execute.  A sharded plan takes only these two calls (paco_execute and
+ * the others return PACO_ERR_UNSUPPORTED).
+ */
+typedef struct {
+    int64_t N1, N2;
+    int b;
+    int G;               /* ranks */
+    int rank;            /* this rank, in [0, G) */
+    int64_t batch;
+    paco_dtype_t dtype;  /* PACO_C64 */
+} paco_shard_opts_t;
+
+paco_status_t paco_plan_create_sharded(paco_plan_t **out, const paco_shard_opts_t *opts);
+/* x_local -> send (Phase I of the rank's slab, packed for the exchange); in != out */
+paco_status_t paco_shard_stage1(paco_plan_t *plan, const void *x_local, void *send, int dir,
+                                paco_stream_t stream);
+/* recv -> y_local (Phase III of the rank's output columns); in != out */
+paco_status_t paco_shard_stage2(paco_plan_t *plan, const void *recv, void *y_local, int dir,
+                                paco_stream_t stream);
 
 /*
  * paco_execute_weighted_power -- paco_execute plus the weighted power of the

@@ -12,6 +12,9 @@ Entry points (same names as the C ABI):
 * ``fft(x, N1, N2, b, p=0, dir=-1)`` -- torch tensors on the GPU.
 * ``PacoFFT`` -- ``torch.autograd.Function`` whose backward is the conjugate
   transform (``dir=+1``).
+* ``sharded`` -- the sharded form across G ranks (``ShardedPlan``,
+  ``sharded_fft``: Phase I per rank, one all-to-all of N/G^2-item blocks,
+  Phase III per rank).
 * ``weighted_power_loss(x, w, N1, N2, b)`` -- sum(w |F x|^2) with the loss
   summed in the Phase III kernel and its backward fused into the conjugate
   transform's loads (``paco_execute_weighted_power`` / ``_input``).
@@ -80,6 +83,15 @@ class PlanInfo(ctypes.Structure):
         ("stage_tile_w", ctypes.c_int * 2), ("stage_cluster", ctypes.c_int * 2),
         ("stage_threads", ctypes.c_int * 2), ("stage_smem", ctypes.c_int * 2),
         ("fused_cluster", ctypes.c_int),
+        ("shard_G", ctypes.c_int),
+        ("shard_rank", ctypes.c_int),
+    ]
+
+
+class ShardOpts(ctypes.Structure):
+    _fields_ = [
+        ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("b", ctypes.c_int), ("G", ctypes.c_int),
+        ("rank", ctypes.c_int), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
     ]
 
 
@@ -138,6 +150,12 @@ def _load():
     L.paco_execute_weighted_power.restype = i32
     L.paco_execute_weighted_input.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, i32, vp]
     L.paco_execute_weighted_input.restype = i32
+    L.paco_plan_create_sharded.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ShardOpts)]
+    L.paco_plan_create_sharded.restype = i32
+    for name in ("paco_shard_stage1", "paco_shard_stage2"):
+        f = getattr(L, name)
+        f.argtypes = [vp, vp, vp, i32, vp]
+        f.restype = i32
     L.paco_noalloc_check.argtypes = []
     L.paco_noalloc_check.restype = i32
     L.paco_debug_noalloc_set_waits.argtypes = [ctypes.c_uint, ctypes.c_uint]

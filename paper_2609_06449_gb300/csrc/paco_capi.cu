@@ -28,6 +28,7 @@ const void *stage_kernel_fn_f64(int lgL, int minb);
 const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_terms_f32(int lgL, int minb);
+const void *stage_kernel_fn_shard_f32(int lgL, int minb);
 } // namespace paco
 
 using namespace paco;
@@ -140,8 +141,8 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
                                  int req_w, int req_k)
 {
     sc->lgL = lgL;
-    if (!pl->form && pl->esize == 8 && lgL == 14 && (mode == 1 || mode == 2) && C >= kPanelWidth &&
-        req_w == 0 && req_k == 0) {
+    if (!pl->form && !pl->shard_G && pl->esize == 8 && lgL == 14 && (mode == 1 || mode == 2) &&
+        C >= kPanelWidth && req_w == 0 && req_k == 0) {
         sc->panel = 1;
         sc->P = kPanelWidth;
         sc->fn = panel_kernel_fn(mode, pl->b);
@@ -195,6 +196,13 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
     if (two) sc->fn = stage_kernel_fn_f32(lgL, 2);
     PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        227 * 1024));
+    if (pl->shard_G && mode != 3) {
+        // the sharded form's variant of the generic kernel (block addresses)
+        sc->fn = stage_kernel_fn_shard_f32(lgL, (two || !generic) ? 2 : 1);
+        if (!sc->fn || B == 1) return fail(PACO_ERR_UNSUPPORTED, "sharded form: stage length 2^%d is not built", lgL);
+        PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        return PACO_OK;
+    }
     if (!pl->form && pl->esize == 8 && B > 1) {
         // the weighted-loss variant of the generic kernel (runtime tile width and
         // cluster size, so it also stands in for a specialised kernel)
@@ -206,7 +214,7 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
     return PACO_OK;
 }
 
-static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
+static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int shard_G = 0, int shard_rank = 0)
 {
     *out = nullptr;
     if (!o) return fail(PACO_ERR_INVALID_ARG, "opts is NULL");
@@ -244,6 +252,8 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
     pl->b = o->b; pl->t = t; pl->p = p; pl->m1 = m1; pl->m2 = m2;
     pl->dtype = o->dtype;
     pl->esize = (o->dtype == PACO_C128) ? 16 : 8;
+    pl->shard_G = shard_G;
+    pl->shard_rank = shard_rank;
     pl->req_ctas = o->ctas_per_sm;
     pl->form = (o->dtype == PACO_C64_TC_BF16X3) ? TC_BF16X3 : (o->dtype == PACO_C64_TC_FP16) ? TC_FP16 : TC_NONE;
     if (pl->form) {
@@ -256,9 +266,11 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
     cudaGetDevice(&pl->device);
 
     paco_status_t st;
-    if ((st = setup_stage(pl, &pl->st[0], l1, pl->N2, 1, o->tile_w, o->cluster)) != PACO_OK ||
+    const int64_t C1 = shard_G ? pl->N2 / shard_G : pl->N2;   // columns of each stage's matrix
+    const int64_t C2 = shard_G ? pl->N1 / shard_G : pl->N1;
+    if ((st = setup_stage(pl, &pl->st[0], l1, C1, 1, o->tile_w, o->cluster)) != PACO_OK ||
         (st = setup_stage(pl, &pl->ph1, l1, pl->N2, 3, o->tile_w, o->cluster)) != PACO_OK ||
-        (st = setup_stage(pl, &pl->st[1], l2, pl->N1, 2, o->tile_w, o->cluster)) != PACO_OK) {
+        (st = setup_stage(pl, &pl->st[1], l2, C2, 2, o->tile_w, o->cluster)) != PACO_OK) {
         paco_plan_destroy(pl);
         return st;
     }
@@ -275,7 +287,7 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o)
         return st;
     }
     cudaDeviceGetAttribute(&pl->num_sms, cudaDevAttrMultiProcessorCount, pl->device);
-    if (cluster_eligible(pl)) {
+    if (!shard_G && cluster_eligible(pl)) {
         if ((st = cluster_setup(pl)) != PACO_OK) {
             paco_plan_destroy(pl);
             return st;
@@ -361,6 +373,8 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
     info->h = pl->N / p - pl->N / (p * p);
     info->mu = pl->N - pl->N / p;
     info->fused_cluster = pl->fused;
+    info->shard_G = pl->shard_G;
+    info->shard_rank = pl->shard_rank;
     for (int s = 0; s < 2; ++s) {
         info->stage_tile_w[s] = 1 << pl->st[s].lgW;
         info->stage_cluster[s] = 1 << pl->st[s].lgK;
@@ -489,6 +503,7 @@ static paco_status_t check_exec(const paco_plan *pl, const void *in, const void 
                                 bool allow_inplace)
 {
     if (!pl) return fail(PACO_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->shard_G) return fail(PACO_ERR_UNSUPPORTED, "a sharded plan runs through paco_shard_stage1 / stage2");
     if (dir != -1 && dir != 1) return fail(PACO_ERR_INVALID_ARG, "dir=%d must be -1 or +1", dir);
     if (pl->batch == 0) return PACO_OK;
     if (!in || !out) return fail(PACO_ERR_INVALID_ARG, "NULL buffer");
@@ -518,6 +533,109 @@ extern "C" paco_status_t paco_execute(paco_plan_t *pl, const void *in, void *out
     if (pl->fused) return launch_cluster(pl, in, out, dir, nullptr, s);
     if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s)) != PACO_OK) return st;
     return launch_stage(pl, pl->st[1], 2, out, out, dir, s);
+}
+
+// ---------------------------------------------------------------------------
+// sharded form (Sect. 4.2, App. C.5 across G ranks)
+// ---------------------------------------------------------------------------
+extern "C" paco_status_t paco_plan_create_sharded(paco_plan_t **out, const paco_shard_opts_t *o)
+{
+    if (!out || !o) return fail(PACO_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (o->dtype != PACO_C64) return fail(PACO_ERR_UNSUPPORTED, "sharded form: complex64 only");
+    const int t = (o->b == 2 || o->b == 4 || o->b == 8 || o->b == 16) ? ilog2_exact(o->b) : -1;
+    if (t < 0) return fail(PACO_ERR_INVALID_ARG, "radix b=%d must be 2, 4, 8 or 16", o->b);
+    const int lg = ilog2_exact(o->G);
+    if (o->G < 2 || lg < 0 || lg % t || o->G > o->N1 || o->G > o->N2 || o->N1 % o->G || o->N2 % o->G)
+        return fail(PACO_ERR_INVALID_ARG, "G=%d must be a power of b=%d with 2 <= G, G | N1, G | N2", o->G, o->b);
+    if (o->N2 / o->G < o->b) return fail(PACO_ERR_INVALID_ARG, "G=%d leaves fewer than b=%d columns per rank", o->G, o->b);
+    if (o->rank < 0 || o->rank >= o->G) return fail(PACO_ERR_INVALID_ARG, "rank %d not in [0, %d)", o->rank, o->G);
+    if (o->batch < 0 || o->batch > 65535) return fail(PACO_ERR_INVALID_ARG, "batch %lld not in [0, 65535]", (long long)o->batch);
+    paco_plan_opts_t po;
+    memset(&po, 0, sizeof(po));
+    po.N1 = o->N1; po.N2 = o->N2; po.b = o->b; po.p = o->G; po.batch = o->batch; po.dtype = o->dtype;
+    return plan_build(out, &po, o->G, o->rank);
+}
+
+static paco_status_t launch_shard(const paco_plan *pl, int mode, const void *in, void *out, int dir,
+                                  cudaStream_t stream)
+{
+    const StageCfg &sc = pl->st[mode == 1 ? 0 : 1];
+    const int64_t G = pl->shard_G, Cl = pl->N2 / G, K1 = pl->N1 / G;
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.out = out;
+    a.lgW = sc.lgW;
+    a.lgK = sc.lgK;
+    a.mode = mode;
+    a.rev_t = pl->t;
+    a.rev_bits = ilog2_exact(Cl);                  // the digit reversal of a rank's local columns / rows
+    a.conj = (dir == 1);
+    a.N_mask = (unsigned)(pl->N - 1);
+    a.twN_lo = pl->twN_lo;
+    a.twN_hi = pl->twN_hi;
+    a.twN_lo_bits = pl->twN_lo_bits;
+    a.pad = (mode == 1) ? 1 : (1 << sc.lgW);
+    if (mode == 1) { a.C = (int)Cl; a.twL = pl->twL1; a.out_ld = (int)K1; }
+    else { a.C = (int)K1; a.twL = pl->twL2; a.out_ld = (int)K1; }
+    ShardArgs sh;
+    memset(&sh, 0, sizeof(sh));
+    sh.c_base = (long long)pl->shard_rank * Cl;
+    sh.lgCl = ilog2_exact(Cl);
+    sh.lgK1 = ilog2_exact(K1);
+    sh.bat_blk = (long long)pl->batch * Cl * K1;
+    sh.bat_Cl = (long long)pl->batch * Cl;
+    long long in_stride = (mode == 1) ? pl->N / G : Cl * K1;
+    long long out_stride = (mode == 1) ? Cl * K1 : pl->N / G;
+    const int K = 1 << sc.lgK;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(sc.ntiles * K), (unsigned)pl->batch, 1);
+    cfg.blockDim = dim3((unsigned)sc.threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)sc.smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    void *params[] = {&a, &sh, &in_stride, &out_stride};
+    PACO_CUDA_TRY(cudaLaunchKernelExC(&cfg, sc.fn, params));
+    return PACO_OK;
+}
+
+static paco_status_t check_shard(const paco_plan *pl, const void *in, const void *out, int dir, const char *fn)
+{
+    if (!pl) return fail(PACO_ERR_INVALID_ARG, "plan is NULL");
+    if (!pl->shard_G) return fail(PACO_ERR_UNSUPPORTED, "%s takes a sharded plan (paco_plan_create_sharded)", fn);
+    if (dir != -1 && dir != 1) return fail(PACO_ERR_INVALID_ARG, "dir=%d must be -1 or +1", dir);
+    if (pl->batch == 0) return PACO_OK;
+    if (!in || !out) return fail(PACO_ERR_INVALID_ARG, "NULL buffer");
+    if (((uintptr_t)in | (uintptr_t)out) & 15u) return fail(PACO_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    if (overlap(in, out, (size_t)(pl->N / pl->shard_G * pl->batch) * pl->esize))
+        return fail(PACO_ERR_ALIASING, "input and output overlap");
+    return PACO_OK;
+}
+
+extern "C" paco_status_t paco_shard_stage1(paco_plan_t *pl, const void *x_local, void *send, int dir,
+                                           paco_stream_t stream)
+{
+    paco_status_t st = check_shard(pl, x_local, send, dir, "paco_shard_stage1");
+    if (st != PACO_OK || pl->batch == 0) return st;
+    set_device(pl);
+    return launch_shard(pl, 1, x_local, send, dir, (cudaStream_t)stream);
+}
+
+extern "C" paco_status_t paco_shard_stage2(paco_plan_t *pl, const void *recv, void *y_local, int dir,
+                                           paco_stream_t stream)
+{
+    paco_status_t st = check_shard(pl, recv, y_local, dir, "paco_shard_stage2");
+    if (st != PACO_OK || pl->batch == 0) return st;
+    set_device(pl);
+    return launch_shard(pl, 2, recv, y_local, dir, (cudaStream_t)stream);
 }
 
 // Plans whose two stages are the generic stage kernels take the weighted terms.

@@ -191,6 +191,17 @@ struct StageArgs {
     const void *tc;         // tensor-core forms: fragment table (paco_tc.cuh)
 };
 
+// The sharded form (paco_plan_create_sharded): rank `rank` of G holds input
+// columns [rank Cl, (rank+1) Cl) of X (Cl = N2/G) and output columns
+// [rank K1, (rank+1) K1) of Y (K1 = N1/G); blocks of N/G^2 items travel
+// between ranks, buffers laid out [G][batch][Cl][K1] (block for / from rank g).
+struct ShardArgs {
+    long long c_base;       // rank * Cl: global column of local column 0 (Phase I twiddle)
+    int lgCl, lgK1;         // log2 Cl, log2 K1
+    long long bat_blk;      // batch * Cl * K1: stride between the blocks of two ranks
+    long long bat_Cl;       // batch * Cl: the same in rows of K1 items
+};
+
 // Element-wise terms of a weighted power loss, taken by the stage kernels
 // built with them (paco_stage_kernel_terms); nullptr switches a term off.
 struct StageTerms {

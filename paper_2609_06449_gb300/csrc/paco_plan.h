@@ -49,6 +49,8 @@ struct paco_plan {
     void *tc = nullptr;            // its fragment table
     int fused = 0;                 // 1: paco_execute is one cluster launch (paco_cluster.cu)
     void *twN_full = nullptr;      // one-launch form: w_N^{-r}, r < N
+    int shard_G = 0;               // sharded form (paco_plan_create_sharded): ranks, 0 = not sharded
+    int shard_rank = 0;
     // uneven batch (paco_plan_create_batched): N = total elements, batch = 1
     paco::BatchedState *bs = nullptr;
 };

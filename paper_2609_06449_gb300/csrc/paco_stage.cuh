@@ -108,9 +108,15 @@ __host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int 
 // FORM != TC_NONE computes the radix-16 passes (F1 and F2 pass 1 when the
 // radix is 16) as tensor-core contractions (paco_tc.cuh); its fragment table
 // and per-warp staging follow the stage's shared memory.
-template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE, bool TERMS = false>
+// TERMS: the weighted-loss terms (StageTerms) are compiled in.  SHARD: the
+// sharded form's addresses (ShardArgs): Phase I on a local input slab with
+// global twiddle columns, stored into the G send blocks; Phase III reading
+// the received blocks; the output offset of the transform is boff_out.
+template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE, bool TERMS = false,
+          bool SHARD = false>
 __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long long boff, int rank,
-                                           unsigned char *smem_raw, const StageTerms *terms = nullptr)
+                                           unsigned char *smem_raw, const StageTerms *terms = nullptr,
+                                           const ShardArgs *sh = nullptr, long long boff_out = 0)
 {
     using C = cx<R>;
     constexpr int L = A * B;
@@ -181,12 +187,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                     // E1 is [col][k_lo]: the epilogue reads it with k_lo fastest
                     const int lgAk = ilog2c<A>::value - lgK;
                     const unsigned klo = (unsigned)(rank * Ak + (e & (Ak - 1)));
-                    const unsigned c = (unsigned)(c0 + (e >> lgAk));
+                    unsigned c = (unsigned)(c0 + (e >> lgAk));
+                    if constexpr (SHARD) c += (unsigned)sh->c_base;
                     r = (klo * c) & args.N_mask;
                 } else {
                     const int e2 = e - nE1;
                     const unsigned khi = (unsigned)(e2 >> lgW);
-                    const unsigned c = (unsigned)(c0 + (e2 & (W - 1)));
+                    unsigned c = (unsigned)(c0 + (e2 & (W - 1)));
+                    if constexpr (SHARD) c += (unsigned)sh->c_base;
                     r = ((unsigned)A * khi * c) & args.N_mask;
                 }
                 E1[e] = cmul(ldg_cx(nlo + (r & lomask)), ldg_cx(nhi + (r >> args.twN_lo_bits)));
@@ -217,8 +225,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
 #pragma unroll
             for (int r = 0; r < RA1; ++r) {
                 const int j = (jj + RA2 * r) * B + jlo;       // logical row in [L]
-                const unsigned row = (mode == 2) ? digit_reverse((unsigned)j, args.rev_bits, args.rev_t)
-                                                 : (unsigned)j;
+                unsigned row = (mode == 2) ? digit_reverse((unsigned)j, args.rev_bits, args.rev_t)
+                                           : (unsigned)j;
+                if constexpr (SHARD) {
+                    // W row pi_m2(j), j = jh Cl + jl, is row pi(jl) of the block from rank jh
+                    if (mode == 2)
+                        row = (unsigned)((long long)(j >> sh->lgCl) * sh->bat_Cl) +
+                              digit_reverse((unsigned)j & ((1u << sh->lgCl) - 1u), args.rev_bits, args.rev_t);
+                }
                 C x = LDCG ? ldcg_cx(gin + (long long)row * args.C + c0 + col)
                            : ldg_cx(gin + (long long)row * args.C + c0 + col);
                 if constexpr (TERMS) if (ldw) {
@@ -335,7 +349,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
 
     // ---- F2 pass 1: radix RB1 over j_lo, span RB2
     constexpr int NB1 = EPT / RB1;
-    C *gout = reinterpret_cast<C *>(args.out) + boff;
+    C *gout = reinterpret_cast<C *>(args.out) + (SHARD ? boff_out : boff);
 #pragma unroll
     for (int u = 0; u < NB1; ++u) {
         const int bfi = tid + NT * u;
@@ -446,7 +460,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             if (mode == 1) {
                 y = cmul(y, cmul(E1[(col << (ilog2c<A>::value - lgK)) + al], E2[(khi << lgW) + col]));
                 const unsigned urow = digit_reverse((unsigned)c, args.rev_bits, args.rev_t);
-                idx = (long long)urow * args.out_ld + kk;
+                if constexpr (SHARD) {
+                    // block for the rank that owns k1 = kk, row pi(c) of the local columns
+                    idx = (long long)(kk >> sh->lgK1) * sh->bat_blk + ((long long)urow << sh->lgK1) +
+                          (kk & ((1 << sh->lgK1) - 1));
+                } else {
+                    idx = (long long)urow * args.out_ld + kk;
+                }
             } else if (mode == 2) {
                 idx = (long long)kk * args.out_ld + c;
                 if constexpr (TERMS) if (stw) wpow += R(wv[k]) * (y.x * y.x + y.y * y.y);
@@ -487,6 +507,20 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel(const StageArgs a
     if ((1 << lgK) > 1) rank = (int)cg::this_cluster().block_rank();
     stage_tile<R, A, B, LGWC, LGKC, MC, false, FORM>(args, (int)(blockIdx.x >> lgK),
                                                      (long long)blockIdx.y * args.batch_stride, rank, smem_raw);
+}
+
+// The generic stage in the sharded form's addresses (ShardArgs): blockIdx.y =
+// transform b; its input is at b * in_stride, its output at b * out_stride.
+template <typename R, int A, int B, int MINB>
+__global__ void __launch_bounds__(512, MINB) paco_stage_kernel_shard(const StageArgs args, const ShardArgs sh,
+                                                                    long long in_stride, long long out_stride)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int rank = 0;
+    if ((1 << args.lgK) > 1) rank = (int)cg::this_cluster().block_rank();
+    stage_tile<R, A, B, -1, -1, 0, false, TC_NONE, false, true>(
+        args, (int)(blockIdx.x >> args.lgK), (long long)blockIdx.y * in_stride, rank, smem_raw, nullptr, &sh,
+        (long long)blockIdx.y * out_stride);
 }
 
 // The generic stage with the element-wise terms of a weighted power loss

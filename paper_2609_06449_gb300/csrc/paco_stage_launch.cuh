@@ -26,6 +26,26 @@ struct StageKernel {
     }
 };
 
+// The sharded-form stage kernel for length 2^lgL.
+template <typename R>
+const void *stage_kernel_fn_shard(int lgL, int minb)
+{
+#define PACO_SHARD_CASE(LG)                                                                          \
+    case LG: {                                                                                       \
+        constexpr int A_ = 1 << (((LG) + 1) / 2), B_ = 1 << ((LG) / 2);                              \
+        if (minb == 2 && sizeof(R) == 4)                                                             \
+            return reinterpret_cast<const void *>(&paco_stage_kernel_shard<R, A_, B_, 2>);           \
+        return reinterpret_cast<const void *>(&paco_stage_kernel_shard<R, A_, B_, 1>);               \
+    }
+    switch (lgL) {
+        PACO_SHARD_CASE(2) PACO_SHARD_CASE(3) PACO_SHARD_CASE(4) PACO_SHARD_CASE(5) PACO_SHARD_CASE(6)
+        PACO_SHARD_CASE(7) PACO_SHARD_CASE(8) PACO_SHARD_CASE(9) PACO_SHARD_CASE(10) PACO_SHARD_CASE(11)
+        PACO_SHARD_CASE(12) PACO_SHARD_CASE(13) PACO_SHARD_CASE(14)
+    default: return nullptr;
+    }
+#undef PACO_SHARD_CASE
+}
+
 // The generic stage kernel for length 2^lgL; TERMS = true: the variant with
 // the weighted-loss terms (StageArgs::ld_w, st_w) compiled in.
 template <typename R, bool TERMS = false>
