@@ -69,10 +69,10 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["B", "A", "B128", "C", "D", "E", "U"], default="B")
+    ap.add_argument("--workload", choices=["B", "A", "B128", "C", "D", "E", "U", "T"], default="B")
     ap.add_argument("--small", action="store_true",
                     help="a reduced case of the workload (C: 1024 lengths to 2^26 + 4096 x 2^12; D: batch 2; "
-                         "U: N = 2^26), for ncu captures")
+                         "U: N = 2^26; T: 2^24 points), for ncu captures")
     ap.add_argument("--no-autotune", action="store_true", help="C: fixed configuration instead of autotuning")
     ap.add_argument("--form", choices=["all", "plain", "bf16x3", "fp16"], default="all",
                     help="D: time only this precision form")
@@ -664,6 +664,53 @@ def run_other(args, ranks, local):
         line["e2e"] = None if args.no_e2e else e2e_host(lambda: pl.execute_host(xh, ho, di, y, -1, stream), max(args.e2e_steps, 1),
                                stream, flop / 1e9, "GFLOP/s", N * B * 8, N * B * 8,
                                "paco_execute_host (pinned host buffers)", mor, world, ranks.barrier)
+    elif wl == "T":
+        # the 128-point DFT sub-pass of a 2^14 stage: tcgen05 BF16x3 against the plain FP32 kernel
+        Bt, Ct = (8, 16384) if args.small else (128, 16384)
+        npts = Bt * 128 * Ct
+        xh = torch.from_numpy(uniform(npts, rank, np.complex64)).pin_memory()
+        x = xh.cuda().reshape(Bt, 128, Ct)
+        y = torch.empty_like(x)
+        y2 = torch.empty_like(x)
+        plan = paco.Plan(128, Ct, 2, Bt, paco.C64)             # Phase I alone: the same column DFTs
+        tot, per, clocks = timed(lambda: paco.probe_tc05_dft128(x, y, Bt, Ct, stream))
+        ptot, pper = time_steps(lambda: plan.execute_phase1(x, y2, -1, stream), K, 3, stream)
+        plan.check()
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(1234)
+        jj = np.arange(128)
+        F = np.exp(-2j * np.pi * np.outer(jj, jj) / 128)
+        rev = np.array([int(f"{k:07b}"[::-1], 2) for k in range(128)])   # Phase I stores row pi(k) (b = 2)
+        e_tc, e_pl = [], []
+        for _ in range(64):
+            bi, ci = int(rng.integers(Bt)), int(rng.integers(Ct))
+            ref = F @ x[bi, :, ci].cpu().numpy().astype(np.complex128)
+            e_tc.append(np.linalg.norm(y[bi, :, ci].cpu().numpy() - ref) / np.linalg.norm(ref))
+            e_pl.append(np.linalg.norm(y2[bi, rev, ci].cpu().numpy() - ref) / np.linalg.norm(ref))
+        ms = mor(statistics.median(per))
+        pms = mor(statistics.median(pper))
+        gbs = lambda t: 16.0 * npts / (t * 1e-3) / 1e9
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                peaks = json.load(fh)
+        except (OSError, ValueError):
+            pass
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+        mma_tflops = 3072.0 * npts / (ms * 1e-3) / 1e12          # 12 real 128 x 128 products per point, 2 flops each
+        line = dict(base, value=gbs(ms), unit="GB/s effective (16 B per point), tcgen05 BF16x3 sub-pass",
+                    higher_is_better=True, ms_per_step=ms, dtype="bf16x3 (fp32 in/out)",
+                    config={"workload": f"DFT-128 sub-pass of a 2^14 stage: {Bt} x [128 x {Ct}] c64 "
+                                        f"({npts} points), tcgen05 BF16x3 vs the plain FP32 stage kernel",
+                            "input": "Re, Im i.i.d. U[-1,1), seed = rank", "l2": "inputs larger than L2"},
+                    forms={"tcgen05_bf16x3": {"ms": ms, "gbs": gbs(ms), "rel_l2_max": float(max(e_tc))},
+                           "plain_fp32": {"ms": pms, "gbs": gbs(pms), "rel_l2_max": float(max(e_pl))}},
+                    accuracy={"measured_on": "64 sampled sequences vs their FP64 DFT"},
+                    roofline={"bound": "tensor", "kernel": "tc05_dft128_kernel", "achieved": mma_tflops,
+                              "peak": bf16_peak, "peak_source": "measured" if peaks else "fallback",
+                              "unit": "TFLOP/s (bf16 MMA work)", "frac": mma_tflops / bf16_peak, "traffic": None,
+                              "hbm": hbm_roofline("tc05_dft128_kernel", 16.0 * npts, ms)},
+                    e2e=None, cpu_baseline=None, gpu_launches=K, clocks=clocks)
     elif wl == "U":
         lg = 13 if args.small else 14
         N1 = N2 = 1 << lg

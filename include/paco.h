@@ -212,6 +212,20 @@ paco_status_t paco_shard_stage2(paco_plan_t *plan, const void *recv, void *y_loc
                                 paco_stream_t stream);
 
 /*
+ * paco_probe_tc05_dft128 -- measurement probe (the paper has no
+ * counterpart): the 128-point DFT sub-pass of a 2^14 stage on the tcgen05
+ * tensor cores, y[b][k][c] = sum_j w_128^{-jk} x[b][j][c] for every b < batch,
+ * k < 128, c < C (complex64, [batch][128][C], device, 16-byte aligned, C a
+ * multiple of 64, in != out), as a BF16x3 complex GEMM with FP32 accumulators
+ * in tensor memory (relative error about 1e-5: the operands are kept to
+ * about 2^-17).  With ms != NULL the call waits and returns the kernel's
+ * CUDA-event time; a wait for the tensor-core operations that gives up
+ * returns PACO_ERR_TIMEOUT.  Builds its 128 KiB operand table on first use.
+ */
+paco_status_t paco_probe_tc05_dft128(const void *x, void *y, int64_t batch, int64_t C, float *ms,
+                                     paco_stream_t stream);
+
+/*
  * paco_execute_weighted_power -- paco_execute plus the weighted power of the
  * result, for a spectral loss: out = y = F^dir x as paco_execute computes it,
  * and *loss = sum over the whole batch of w[n] |y[n]|^2, accumulated by the

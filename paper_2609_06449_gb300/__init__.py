@@ -156,6 +156,8 @@ def _load():
         f = getattr(L, name)
         f.argtypes = [vp, vp, vp, i32, vp]
         f.restype = i32
+    L.paco_probe_tc05_dft128.argtypes = [vp, vp, i64, i64, ctypes.POINTER(ctypes.c_float), vp]
+    L.paco_probe_tc05_dft128.restype = i32
     L.paco_noalloc_check.argtypes = []
     L.paco_noalloc_check.restype = i32
     L.paco_debug_noalloc_set_waits.argtypes = [ctypes.c_uint, ctypes.c_uint]
@@ -364,6 +366,16 @@ def get_plan(N1: int, N2: int, b: int, batch: int, dtype: int, p: int = 0,
             pl = Plan(N1, N2, b, batch, dtype, p)
         _PLANS[key] = pl
     return pl
+
+
+def probe_tc05_dft128(x, y, batch: int, C: int, stream=None, timed: bool = False):
+    """``paco_probe_tc05_dft128``: y[b][k][c] = sum_j w_128^{-jk} x[b][j][c] on
+    the tcgen05 tensor cores (BF16x3).  Returns the kernel time in ms when
+    ``timed`` (the call then waits), else None."""
+    ms = ctypes.c_float(0.0)
+    _check(lib.paco_probe_tc05_dft128(_ptr(x), _ptr(y), int(batch), int(C),
+                                      ctypes.byref(ms) if timed else None, _stream(stream)))
+    return ms.value if timed else None
 
 
 def fft(x, N1: int, N2: int, b: int, p: int = 0, dir: int = -1, out=None):
