@@ -95,7 +95,11 @@ paco_status_t paco::gen_table(int esize, void **dst, long long M, long long coun
 }
 
 // Tile width W and cluster size K for a stage of length 2^lgL over C columns:
-// about 64 KiB of tile per CTA, at least 32 B per row segment.
+// about 64 KiB of tile per CTA, at least 32 B per row segment, and at most
+// 16 columns for L >= 128, 64 for L = 32, 64, none for L <= 16 (measured on
+// GB300, one 2^28-point complex64 pass: L = 16 4.04 -> 1.02 ms with 512
+// columns instead of 16; L = 32 1.76 -> 0.79 ms and L = 64 0.97 -> 0.76 ms
+// with 64; L = 128 and 256 are fastest with 16).
 static void choose_tile(const paco_plan *pl, int lgL, int64_t C, int req_w, int req_k, int mode,
                         int *lgW_out, int *lgK_out)
 {
@@ -108,7 +112,8 @@ static void choose_tile(const paco_plan *pl, int lgL, int64_t C, int req_w, int 
         int lgWmin = 5 - lgE;                        // 32-byte rows: 4 (c64) / 2 (c128)
         lgW = lgBudget - lgL;
         if (lgW < lgWmin) lgW = lgWmin;
-        if (lgW > 4) lgW = 4;                        // at most 16 columns
+        const int lgWmax = (lgL <= 4) ? lgBudget : (lgL <= 6) ? 6 : 4;
+        if (lgW > lgWmax) lgW = lgWmax;
     }
     if (lgW > lgC) lgW = lgC;
     if (lgW < 0) lgW = 0;
