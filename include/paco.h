@@ -109,6 +109,8 @@ typedef struct {
                                     cluster launch (see paco_execute) */
     int shard_G;                 /* sharded plan: G ranks (0: not sharded) */
     int shard_rank;              /* sharded plan: this rank */
+    int stage_split[2];          /* 1: the stage runs as two passes through the plan's
+                                    N * batch scratch (complex64 stages of 2^12, 2^13) */
 } paco_plan_info_t;
 
 /*

@@ -85,6 +85,7 @@ class PlanInfo(ctypes.Structure):
         ("fused_cluster", ctypes.c_int),
         ("shard_G", ctypes.c_int),
         ("shard_rank", ctypes.c_int),
+        ("stage_split", ctypes.c_int * 2),
     ]
 
 

@@ -29,6 +29,7 @@ const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_terms_f32(int lgL, int minb);
 const void *stage_kernel_fn_shard_f32(int lgL, int minb);
+const void *stage_kernel_fn_split_f32(int lgL, int minb);
 } // namespace paco
 
 using namespace paco;
@@ -142,6 +143,47 @@ static void choose_tile(const paco_plan *pl, int lgL, int64_t C, int req_w, int 
 static const int kPanelWidth = 128;
 static const bool kDefaultTwoCtas = true;
 
+// A complex64 stage of length 2^12 or 2^13 runs as two passes through the
+// plan's scratch: the single-tile kernel at those lengths needs four radix
+// passes and three exchanges per tile, while passes of length 2^6 / 2^7 run
+// near the memory bound (measured on GB300, one 2^28-point pass: L = 64
+// 0.76 ms, L = 128 0.71 ms, against 1.8-2.4 ms for L = 4096 and 3.2 ms for
+// L = 8192 in one pass).
+static paco_status_t setup_split(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode)
+{
+    const int lgLa = (lgL + 1) / 2, lgLb = lgL / 2;
+    const int lgC = ilog2_exact(C);
+    for (int p = 0; p < 2; ++p) {
+        const int lgLs = p == 0 ? lgLa : lgLb;
+        const int64_t Cv = ((int64_t)1 << (p == 0 ? lgLb : lgLa)) * C;   // the pass's view columns
+        int lgW = 0, lgK = 0;
+        choose_tile(pl, lgLs, Cv, 0, 0, 2, &lgW, &lgK);
+        if (lgW > lgC) lgW = lgC;                        // a tile stays inside one column block
+        if (mode == 1 && p == 1 && lgW > lgLa) lgW = lgLa;
+        const int As = 1 << ((lgLs + 1) / 2), Bs = 1 << (lgLs / 2), W = 1 << lgW;
+        const bool fits = lgK == 0 && ((p == 0 && (1 << lgLa) <= (As + Bs) * W) ||
+                                       (p == 1 && (mode == 2 || (1 << lgLb) <= Bs * W)));
+        if (!fits) return PACO_OK;                       // not split: the single-pass kernel runs
+        const int pad = (mode == 1 && p == 0) ? 1 : W;
+        sc->sp_lgW[p] = lgW;
+        sc->sp_threads[p] = (int)(((int64_t)1 << lgLs) * W / 16);
+        sc->sp_smem[p] = stage_smem_elems(As, Bs, 1, W, pad) * pl->esize;
+        sc->sp_ntiles[p] = (int)(Cv / W);
+        const int minb = (pl->req_ctas == 1 || sc->sp_smem[p] > 113 * 1024) ? 1 : 2;
+        sc->sp_fn[p] = stage_kernel_fn_split_f32(lgLs, minb);
+        if (!sc->sp_fn[p] || sc->sp_threads[p] > 512) return PACO_OK;
+        PACO_CUDA_TRY(cudaFuncSetAttribute(sc->sp_fn[p], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    }
+    paco_status_t st;
+    if ((st = gen_table(8, &sc->sp_tw[0], (long long)1 << lgLa, (long long)1 << lgLa, 1, 0)) != PACO_OK ||
+        (st = gen_table(8, &sc->sp_tw[1], (long long)1 << lgLb, (long long)1 << lgLb, 1, 0)) != PACO_OK)
+        return st;
+    sc->lgLa = lgLa;
+    sc->lgLb = lgLb;
+    sc->split = 1;
+    return PACO_OK;
+}
+
 static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode,
                                  int req_w, int req_k)
 {
@@ -207,6 +249,12 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         if (!sc->fn || B == 1) return fail(PACO_ERR_UNSUPPORTED, "sharded form: stage length 2^%d is not built", lgL);
         PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         return PACO_OK;
+    }
+    // (both pass lengths powers of b, so that pi_m2(j_a Lb + j_b) = pi(j_b) La + pi(j_a))
+    if (!pl->form && !pl->shard_G && pl->esize == 8 && (lgL == 12 || lgL == 13) && mode != 3 && req_w == 0 &&
+        req_k == 0 && ((lgL + 1) / 2) % pl->t == 0 && (lgL / 2) % pl->t == 0) {
+        paco_status_t st = setup_split(pl, sc, lgL, C, mode);
+        if (st != PACO_OK) return st;
     }
     if (!pl->form && pl->esize == 8 && B > 1) {
         // the weighted-loss variant of the generic kernel (runtime tile width and
@@ -316,6 +364,13 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
         }
         pl->ctr_words = words;
     }
+    if ((pl->st[0].split || pl->st[1].split) && pl->batch > 0) {
+        cudaError_t ea = cudaMalloc(&pl->split_scratch, (size_t)(pl->N * pl->batch) * pl->esize);
+        if (ea != cudaSuccess) {
+            paco_plan_destroy(pl);
+            return fail(PACO_ERR_NOMEM, "split-stage scratch: %s", cudaGetErrorString(ea));
+        }
+    }
     cudaError_t e = cudaMalloc(&pl->d_status, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -354,6 +409,9 @@ extern "C" void paco_plan_destroy(paco_plan_t *pl)
     cudaFree(pl->twN_lo);
     cudaFree(pl->twN_hi);
     cudaFree(pl->twN_full);
+    cudaFree(pl->split_scratch);
+    for (int k = 0; k < 2; ++k)
+        for (int p = 0; p < 2; ++p) cudaFree(pl->st[k].sp_tw[p]);
     cudaFree(pl->d_status);
     cudaFree(pl->scratch);
     cudaFree(pl->ctr);
@@ -380,6 +438,8 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
     info->fused_cluster = pl->fused;
     info->shard_G = pl->shard_G;
     info->shard_rank = pl->shard_rank;
+    info->stage_split[0] = pl->st[0].split;
+    info->stage_split[1] = pl->st[1].split;
     for (int s = 0; s < 2; ++s) {
         info->stage_tile_w[s] = 1 << pl->st[s].lgW;
         info->stage_cluster[s] = 1 << pl->st[s].lgK;
@@ -429,6 +489,55 @@ static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int m
     return PACO_OK;
 }
 
+// The two passes of a split stage: in -> scratch (pass A), scratch -> out (pass B).
+static paco_status_t launch_split(const paco_plan *pl, const StageCfg &sc, int mode, const void *in, void *out,
+                                  int dir, cudaStream_t stream)
+{
+    const int64_t C = (mode == 1) ? pl->N2 : pl->N1;
+    const int lgC = ilog2_exact(C);
+    for (int p = 0; p < 2; ++p) {
+        const int sub = (mode == 1) ? 1 + p : 3 + p;
+        StageArgs a;
+        memset(&a, 0, sizeof(a));
+        a.batch_stride = pl->N;
+        a.lgW = sc.sp_lgW[p];
+        a.lgK = 0;
+        a.mode = (sub == 1) ? 1 : 2;
+        a.rev_t = pl->t;
+        a.rev_bits = (sub == 3) ? sc.lgLa : sc.lgLb;     // sub 3: rows pi over La's digits (others: natural rows)
+        a.conj = (dir == 1);
+        a.N_mask = (unsigned)(pl->N - 1);
+        a.twN_lo = pl->twN_lo;
+        a.twN_hi = pl->twN_hi;
+        a.twN_lo_bits = pl->twN_lo_bits;
+        a.pad = (sub == 1) ? 1 : (1 << sc.sp_lgW[p]);
+        a.twL = sc.sp_tw[p];
+        a.C = (int)((sub == 1) ? (C << sc.lgLb) : (sub == 2) ? (C << sc.lgLa) : (sub == 3) ? C : (C << sc.lgLa));
+        a.out_ld = (int)((sub == 2) ? ((int64_t)1 << (sc.lgLa + sc.lgLb)) : C);
+        SplitArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.sub = sub;
+        sa.lgC = lgC;
+        sa.lgLa = sc.lgLa;
+        sa.lgLb = sc.lgLb;
+        sa.rev_bits_c = (mode == 1) ? lgC : 0;
+        sa.twS = (mode == 1) ? pl->twL1 : pl->twL2;
+        const void *src = (p == 0) ? in : pl->split_scratch;
+        void *dst = (p == 0) ? pl->split_scratch : out;
+        for (int64_t b0 = 0; b0 < pl->batch; b0 += 65535) {
+            const int64_t nb = (pl->batch - b0 < 65535) ? pl->batch - b0 : 65535;
+            StageArgs ab = a;
+            ab.in = (const char *)src + (size_t)(b0 * pl->N) * pl->esize;
+            ab.out = (char *)dst + (size_t)(b0 * pl->N) * pl->esize;
+            void *params[] = {&ab, &sa};
+            PACO_CUDA_TRY(cudaLaunchKernel(sc.sp_fn[p], dim3((unsigned)sc.sp_ntiles[p], (unsigned)nb, 1),
+                                           dim3((unsigned)sc.sp_threads[p], 1, 1), params, (size_t)sc.sp_smem[p],
+                                           stream));
+        }
+    }
+    return PACO_OK;
+}
+
 static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int mode,
                                   const void *in, void *out, int dir, cudaStream_t stream,
                                   const StageTerms *terms = nullptr)
@@ -439,6 +548,7 @@ static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int m
     }
     if (terms && !sc.fn_terms)
         return fail(PACO_ERR_UNSUPPORTED, "weighted terms: complex64 plans with both factors >= 4 only");
+    if (sc.split && !terms) return launch_split(pl, sc, mode, in, out, dir, stream);
     StageArgs a;
     memset(&a, 0, sizeof(a));
     a.in = in;

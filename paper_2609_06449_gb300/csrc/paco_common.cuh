@@ -202,6 +202,21 @@ struct ShardArgs {
     long long bat_Cl;       // batch * Cl: the same in rows of K1 items
 };
 
+// A stage of length L = La Lb split into two passes through global memory
+// (the local FFT's top split taken out of the CTA: pass A = La-point DFTs
+// with the twiddle w_L^{-k_a j_b}, pass B = Lb-point DFTs with the stage's
+// epilogue), scratch S holding the intermediate.  sub: 1 Phase I pass A
+// (x -> S[j_b][c][k_a]), 2 Phase I pass B (S -> W[pi_m2(c)][k_a + La k_b]
+// with w_N^{-k1 c}), 3 Phase III pass A (W rows pi_m2(j) -> S[j_b][k_a][v]),
+// 4 Phase III pass B (S -> y[k_a + La k_b][v]).
+struct SplitArgs {
+    int sub;
+    int lgC;                // log2 of the stage's column count
+    int lgLa, lgLb;
+    int rev_bits_c;         // sub 2: pi_m2 over log2 N2 bits
+    const void *twS;        // w_L^{-r}, r < L (sub 1, 3)
+};
+
 // Element-wise terms of a weighted power loss, taken by the stage kernels
 // built with them (paco_stage_kernel_terms); nullptr switches a term off.
 struct StageTerms {

@@ -21,6 +21,13 @@ struct StageCfg {
     const void *fn_terms = nullptr;   // the same stage with the weighted-loss terms (complex64), or nullptr
     int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
     int P = 0;        // panel width (columns)
+    // split = 1: the stage runs as two passes through the plan's scratch (pass A
+    // of length 2^lgLa, pass B of length 2^lgLb; SplitArgs in paco_common.cuh)
+    int split = 0;
+    int lgLa = 0, lgLb = 0;
+    int sp_lgW[2] = {0, 0}, sp_threads[2] = {0, 0}, sp_smem[2] = {0, 0}, sp_ntiles[2] = {0, 0};
+    const void *sp_fn[2] = {nullptr, nullptr};
+    void *sp_tw[2] = {nullptr, nullptr};   // w_{2^lgLa}^{-r} and w_{2^lgLb}^{-r}
 };
 
 struct BatchedState;  // paco_batched.cu
@@ -49,6 +56,7 @@ struct paco_plan {
     void *tc = nullptr;            // its fragment table
     int fused = 0;                 // 1: paco_execute is one cluster launch (paco_cluster.cu)
     void *twN_full = nullptr;      // one-launch form: w_N^{-r}, r < N
+    void *split_scratch = nullptr; // split stages: the intermediate of their two passes (N * batch)
     int shard_G = 0;               // sharded form (paco_plan_create_sharded): ranks, 0 = not sharded
     int shard_rank = 0;
     // uneven batch (paco_plan_create_batched): N = total elements, batch = 1

@@ -113,10 +113,11 @@ __host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int 
 // global twiddle columns, stored into the G send blocks; Phase III reading
 // the received blocks; the output offset of the transform is boff_out.
 template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE, bool TERMS = false,
-          bool SHARD = false>
+          bool SHARD = false, bool SPLIT = false>
 __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long long boff, int rank,
                                            unsigned char *smem_raw, const StageTerms *terms = nullptr,
-                                           const ShardArgs *sh = nullptr, long long boff_out = 0)
+                                           const ShardArgs *sh = nullptr, long long boff_out = 0,
+                                           const SplitArgs *sp = nullptr)
 {
     using C = cx<R>;
     constexpr int L = A * B;
@@ -176,7 +177,28 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
         for (int r = tid; r < B; r += NT) twB[r] = ldg_cx(twL + r * A);
         for (int r = tid; r < SL; r += NT) tlo[r] = ldg_cx(twL + r);
         for (int r = tid; r < SH; r += NT) thi[r] = ldg_cx(twL + r * SL);
-        if (mode == 1) {
+        if constexpr (SPLIT) {
+            // one pass of a split stage: the tile's twiddles (its columns share j_b, or c)
+            if (sp->sub == 1 || sp->sub == 3) {
+                const C *twS = reinterpret_cast<const C *>(sp->twS);
+                const int jb = c0 >> sp->lgC;
+                for (int r = tid; r < (1 << sp->lgLa); r += NT) E1[r] = ldg_cx(twS + r * jb);   // w_L^{-k_a j_b}
+            } else if (sp->sub == 2) {
+                const C *nlo = reinterpret_cast<const C *>(args.twN_lo);
+                const C *nhi = reinterpret_cast<const C *>(args.twN_hi);
+                const unsigned lomask = (1u << args.twN_lo_bits) - 1u;
+                const unsigned cw = (unsigned)(c0 >> sp->lgLa), ka0 = (unsigned)(c0 & ((1 << sp->lgLa) - 1));
+                for (int e = tid; e < W; e += NT) {                                          // w_N^{-k_a c}
+                    const unsigned r = ((ka0 + (unsigned)e) * cw) & args.N_mask;
+                    E1[e] = cmul(ldg_cx(nlo + (r & lomask)), ldg_cx(nhi + (r >> args.twN_lo_bits)));
+                }
+                for (int e = tid; e < (1 << sp->lgLb); e += NT) {                             // w_N^{-La k_b c}
+                    const unsigned r = (((unsigned)e << sp->lgLa) * cw) & args.N_mask;
+                    E2[e] = cmul(ldg_cx(nlo + (r & lomask)), ldg_cx(nhi + (r >> args.twN_lo_bits)));
+                }
+            }
+        }
+        if (!SPLIT && mode == 1) {
             const C *nlo = reinterpret_cast<const C *>(args.twN_lo);
             const C *nhi = reinterpret_cast<const C *>(args.twN_hi);
             const unsigned lomask = (1u << args.twN_lo_bits) - 1u;
@@ -213,6 +235,15 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
         if (ldw) lds = R(terms->ld_mult) * (terms->ld_scale ? R(__ldg(terms->ld_scale)) : R(1));
     }
 
+    // split pass A of Phase III: the tile's column block j_b lies in W's row block pi(j_b)
+    [[maybe_unused]] long long cbase = 0;
+    if constexpr (SPLIT) {
+        cbase = c0;
+        if (sp->sub == 3)
+            cbase = ((long long)digit_reverse((unsigned)(c0 >> sp->lgC), sp->lgLb, args.rev_t) << (sp->lgLa + sp->lgC)) +
+                    (c0 & ((1 << sp->lgC) - 1));
+    }
+
     // ---- F1 pass 1: radix RA1 over j_hi, span RA2; operands straight from HBM
     {
         constexpr int NB = EPT / RA1;
@@ -233,8 +264,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                         row = (unsigned)((long long)(j >> sh->lgCl) * sh->bat_Cl) +
                               digit_reverse((unsigned)j & ((1u << sh->lgCl) - 1u), args.rev_bits, args.rev_t);
                 }
-                C x = LDCG ? ldcg_cx(gin + (long long)row * args.C + c0 + col)
-                           : ldg_cx(gin + (long long)row * args.C + c0 + col);
+                C x;
+                if constexpr (SPLIT) {
+                    if (sp->sub != 3) row = (unsigned)j;               // natural rows (sub 3: pi over La's digits)
+                    x = ldg_cx(gin + (long long)row * args.C + cbase + col);
+                } else {
+                    x = LDCG ? ldcg_cx(gin + (long long)row * args.C + c0 + col)
+                             : ldg_cx(gin + (long long)row * args.C + c0 + col);
+                }
                 if constexpr (TERMS) if (ldw) {
                     const R f = lds * R(__ldg(terms->ld_w + boff + (long long)row * args.C + c0 + col));
                     x.x *= f;
@@ -457,7 +494,24 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             const int kk = klo + A * khi;             // natural frequency in [L]
             C y = v[u * RL + k];
             long long idx;
-            if (mode == 1) {
+            if constexpr (SPLIT) {
+                const int cc = c0 + col;                      // the pass's view column
+                const int mC = (1 << sp->lgC) - 1;
+                if (sp->sub == 1) {                           // S[j_b][c][k_a], view column j_b C + c
+                    y = cmul(y, E1[kk]);
+                    idx = ((long long)cc << sp->lgLa) + kk;
+                } else if (sp->sub == 2) {                    // W[pi_m2(c)][k_a + La k_b], view column c La + k_a
+                    y = cmul(y, cmul(E1[col], E2[kk]));
+                    const unsigned cw = (unsigned)(cc >> sp->lgLa);
+                    idx = (long long)digit_reverse(cw, sp->rev_bits_c, args.rev_t) * args.out_ld +
+                          (cc & ((1 << sp->lgLa) - 1)) + ((long long)kk << sp->lgLa);
+                } else if (sp->sub == 3) {                    // S[j_b][k_a][v], view column j_b C + v
+                    y = cmul(y, E1[kk]);
+                    idx = ((((long long)(c0 >> sp->lgC) << sp->lgLa) + kk) << sp->lgC) + (cc & mC);
+                } else {                                      // y[k_a + La k_b][v], view column k_a C + v
+                    idx = (long long)((cc >> sp->lgC) + (kk << sp->lgLa)) * args.out_ld + (cc & mC);
+                }
+            } else if (mode == 1) {
                 y = cmul(y, cmul(E1[(col << (ilog2c<A>::value - lgK)) + al], E2[(khi << lgW) + col]));
                 const unsigned urow = digit_reverse((unsigned)c, args.rev_bits, args.rev_t);
                 if constexpr (SHARD) {
@@ -521,6 +575,15 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel_shard(const Stage
     stage_tile<R, A, B, -1, -1, 0, false, TC_NONE, false, true>(
         args, (int)(blockIdx.x >> args.lgK), (long long)blockIdx.y * in_stride, rank, smem_raw, nullptr, &sh,
         (long long)blockIdx.y * out_stride);
+}
+
+// One pass of a split stage (SplitArgs); tiles of one CTA (no cluster).
+template <typename R, int A, int B, int MINB>
+__global__ void __launch_bounds__(512, MINB) paco_stage_kernel_split(const StageArgs args, const SplitArgs sp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stage_tile<R, A, B, -1, 0, 0, false, TC_NONE, false, false, true>(
+        args, (int)blockIdx.x, (long long)blockIdx.y * args.batch_stride, 0, smem_raw, nullptr, nullptr, 0, &sp);
 }
 
 // The generic stage with the element-wise terms of a weighted power loss

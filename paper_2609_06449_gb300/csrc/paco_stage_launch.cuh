@@ -46,6 +46,23 @@ const void *stage_kernel_fn_shard(int lgL, int minb)
 #undef PACO_SHARD_CASE
 }
 
+// One pass of a split stage, length 2^lgL (complex64).
+template <typename R>
+const void *stage_kernel_fn_split(int lgL, int minb)
+{
+#define PACO_SPLIT_CASE(LG)                                                                          \
+    case LG: {                                                                                       \
+        constexpr int A_ = 1 << (((LG) + 1) / 2), B_ = 1 << ((LG) / 2);                              \
+        if (minb == 2) return reinterpret_cast<const void *>(&paco_stage_kernel_split<R, A_, B_, 2>); \
+        return reinterpret_cast<const void *>(&paco_stage_kernel_split<R, A_, B_, 1>);               \
+    }
+    switch (lgL) {
+        PACO_SPLIT_CASE(5) PACO_SPLIT_CASE(6) PACO_SPLIT_CASE(7)
+    default: return nullptr;
+    }
+#undef PACO_SPLIT_CASE
+}
+
 // The generic stage kernel for length 2^lgL; TERMS = true: the variant with
 // the weighted-loss terms (StageArgs::ld_w, st_w) compiled in.
 template <typename R, bool TERMS = false>

@@ -153,6 +153,26 @@ def test_one_launch_form_batch_limit():
         assert rel_l2(run(plan, x), oracle.fft(x.astype(np.complex128))) <= 5e-7 * 16
 
 
+@pytest.mark.parametrize("N1,N2,b,batch,split", [
+    (4096, 4096, 4, 2, (1, 1)), (4096, 4096, 2, 1, (1, 1)), (4096, 4096, 8, 1, (1, 1)),
+    (4096, 4096, 16, 1, (0, 0)), (8192, 4096, 2, 1, (1, 1)), (4096, 8192, 2, 1, (1, 1)),
+    (8192, 256, 2, 3, (1, 0)), (256, 8192, 2, 3, (0, 1)), (4096, 64, 4, 5, (1, 0))])
+@pytest.mark.parametrize("d", [-1, 1])
+def test_split_stages_against_oracle(N1, N2, b, batch, split, d):
+    """Stages of 2^12 and 2^13 (complex64) run as two passes through the
+    plan's scratch (pass A of length 2^ceil(l/2) with the twiddle
+    w_L^{-k_a j_b}, pass B with the stage's epilogue); radix 16 at 2^12 keeps
+    the single pass (its half-lengths are not powers of 16).  Every transform
+    element by element against the oracle, both directions."""
+    N = N1 * N2
+    plan = paco.Plan(N1, N2, b, batch, paco.C64)
+    assert tuple(plan.info.stage_split) == split
+    x = uniform(batch * N, N1 + 3 * N2 + b, np.complex64).reshape(batch, N)
+    got = run(plan, x, d)
+    ref = oracle.fft(x.astype(np.complex128), dir=d, threads=0)
+    assert rel_l2(got, ref) <= 5e-7 * math.log2(N), (N1, N2, b)
+
+
 def test_closed_forms_on_gpu():
     """delta -> constant; single tone -> N delta; Parseval."""
     N1 = N2 = 256
