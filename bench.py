@@ -637,8 +637,10 @@ def run_other(args, ranks, local):
             ms = mor(tot) / K
             torch.cuda.synchronize()
             err = rel_l2_vs_oracle(y[:N].cpu().numpy(), xh[:N].numpy())
+            split = tuple(pl.info.stage_split)
             forms[name] = {"ms_per_step": ms, "value": flop * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
-                           "rel_l2_transform0": err, "dominant_launch_ms": statistics.mean(per) / 2}
+                           "rel_l2_transform0": err, "dominant_launch_ms": statistics.mean(per) / 2,
+                           "stage_split": list(split), "launches_per_step": 2 + sum(split)}
             if name == "bf16x3":
                 clocks = ck
             pl.close()
@@ -654,9 +656,11 @@ def run_other(args, ranks, local):
                             "input": "log-uniform magnitudes 1e-4..1e4, uniform phases, seed = 100*rank + i",
                             "l2": "inputs larger than L2"},
                     forms=forms, context=cufft_context(x, N, B, flop),
-                    roofline=hbm_roofline(f"stage kernel ({head})", 16.0 * N * B,
-                                          forms[head]["dominant_launch_ms"]),
-                    e2e=None, cpu_baseline=cpu_leg(args, rank, world), gpu_launches=2 * K * len(forms), clocks=clocks)
+                    roofline=hbm_roofline(f"stage kernel ({head})" + (", two passes per stage"
+                                                                       if sum(forms[head]["stage_split"]) else ""),
+                                          16.0 * N * B, forms[head]["dominant_launch_ms"]),
+                    e2e=None, cpu_baseline=cpu_leg(args, rank, world),
+                    gpu_launches=K * sum(f["launches_per_step"] for f in forms.values()), clocks=clocks)
         # e2e for the form of the line's value
         pl = paco.Plan(N1, N2, 4, B, hdt)
         ho = torch.empty_like(xh).pin_memory()
