@@ -90,6 +90,11 @@ typedef struct {
     int cluster;         /* CTAs per cluster (1, 2, 4, 8); 0 = default */
     int ctas_per_sm;     /* resident CTAs per SM the stage kernels are compiled
                             for (1 or 2; complex64 stage kernels only); 0 = default */
+    int split;           /* complex64 stages of 2^12..2^14 as two passes through
+                            scratch (paco_plan_info.stage_split): 0 = default (2^12,
+                            2^13; 2^14 keeps the L2 panel pipeline), 1 = wherever
+                            possible (2^14 in column chunks that keep the
+                            intermediate in L2), -1 = never */
 } paco_plan_opts_t;
 
 /* Read-only description of a plan (paco_plan_info). */

@@ -70,6 +70,7 @@ class PlanOpts(ctypes.Structure):
         ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("b", ctypes.c_int),
         ("p", ctypes.c_int), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
         ("tile_w", ctypes.c_int), ("cluster", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+        ("split", ctypes.c_int),
     ]
 
 
@@ -225,9 +226,9 @@ class Plan:
     for torch's current stream."""
 
     def __init__(self, N1: int, N2: int, b: int, batch: int = 1, dtype: int = C64,
-                 p: int = 0, tile_w: int = 0, cluster: int = 0, ctas_per_sm: int = 0):
+                 p: int = 0, tile_w: int = 0, cluster: int = 0, ctas_per_sm: int = 0, split: int = 0):
         o = PlanOpts(int(N1), int(N2), int(b), int(p), int(batch), int(dtype),
-                     int(tile_w), int(cluster), int(ctas_per_sm))
+                     int(tile_w), int(cluster), int(ctas_per_sm), int(split))
         h = ctypes.c_void_p()
         _check(lib.paco_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))
         self._h = h

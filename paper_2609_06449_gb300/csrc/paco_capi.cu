@@ -151,14 +151,21 @@ static const bool kDefaultTwoCtas = true;
 // L = 8192 in one pass).
 static paco_status_t setup_split(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode)
 {
-    const int lgLa = (lgL + 1) / 2, lgLb = lgL / 2;
+    // pass lengths: powers of b (so that pi_m2(j_a Lb + j_b) = pi(j_b) La + pi(j_a)),
+    // La the larger, both between 2^5 and 2^8
+    int lgLa = (lgL + 1) / 2;
+    while (lgLa % pl->t) ++lgLa;
+    const int lgLb = lgL - lgLa;
+    if (lgLb % pl->t || lgLb < 5 || lgLa > 8) return PACO_OK;
     const int lgC = ilog2_exact(C);
+    // 2^14: column chunks of 256, whose intermediate (32 MiB a transform) stays in L2
+    const int lgCc = (lgL == 14 && lgC > 8) ? 8 : lgC;
     for (int p = 0; p < 2; ++p) {
         const int lgLs = p == 0 ? lgLa : lgLb;
-        const int64_t Cv = ((int64_t)1 << (p == 0 ? lgLb : lgLa)) * C;   // the pass's view columns
+        const int64_t Cv = ((int64_t)1 << ((p == 0 ? lgLb : lgLa) + lgCc));   // the pass's view columns
         int lgW = 0, lgK = 0;
         choose_tile(pl, lgLs, Cv, 0, 0, 2, &lgW, &lgK);
-        if (lgW > lgC) lgW = lgC;                        // a tile stays inside one column block
+        if (lgW > lgCc) lgW = lgCc;                      // a tile stays inside one column block
         if (mode == 1 && p == 1 && lgW > lgLa) lgW = lgLa;
         const int As = 1 << ((lgLs + 1) / 2), Bs = 1 << (lgLs / 2), W = 1 << lgW;
         const bool fits = lgK == 0 && ((p == 0 && (1 << lgLa) <= (As + Bs) * W) ||
@@ -180,6 +187,7 @@ static paco_status_t setup_split(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         return st;
     sc->lgLa = lgLa;
     sc->lgLb = lgLb;
+    sc->sp_lgCc = lgCc;
     sc->split = 1;
     return PACO_OK;
 }
@@ -189,7 +197,7 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
 {
     sc->lgL = lgL;
     if (!pl->form && !pl->shard_G && pl->esize == 8 && lgL == 14 && (mode == 1 || mode == 2) &&
-        C >= kPanelWidth && req_w == 0 && req_k == 0) {
+        C >= kPanelWidth && req_w == 0 && req_k == 0 && pl->req_split != 1) {
         sc->panel = 1;
         sc->P = kPanelWidth;
         sc->fn = panel_kernel_fn(mode, pl->b);
@@ -250,9 +258,8 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         return PACO_OK;
     }
-    // (both pass lengths powers of b, so that pi_m2(j_a Lb + j_b) = pi(j_b) La + pi(j_a))
-    if (!pl->form && !pl->shard_G && pl->esize == 8 && (lgL == 12 || lgL == 13) && mode != 3 && req_w == 0 &&
-        req_k == 0 && ((lgL + 1) / 2) % pl->t == 0 && (lgL / 2) % pl->t == 0) {
+    if (!pl->form && !pl->shard_G && pl->esize == 8 && pl->req_split >= 0 &&
+        (lgL == 12 || lgL == 13 || (lgL == 14 && pl->req_split == 1)) && mode != 3 && req_w == 0 && req_k == 0) {
         paco_status_t st = setup_split(pl, sc, lgL, C, mode);
         if (st != PACO_OK) return st;
     }
@@ -307,6 +314,7 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
     pl->esize = (o->dtype == PACO_C128) ? 16 : 8;
     pl->shard_G = shard_G;
     pl->shard_rank = shard_rank;
+    pl->req_split = o->split;
     pl->req_ctas = o->ctas_per_sm;
     pl->form = (o->dtype == PACO_C64_TC_BF16X3) ? TC_BF16X3 : (o->dtype == PACO_C64_TC_FP16) ? TC_FP16 : TC_NONE;
     if (pl->form) {
@@ -365,7 +373,17 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
         pl->ctr_words = words;
     }
     if ((pl->st[0].split || pl->st[1].split) && pl->batch > 0) {
-        cudaError_t ea = cudaMalloc(&pl->split_scratch, (size_t)(pl->N * pl->batch) * pl->esize);
+        size_t elems = 0;                                // whole stages: N a transform; chunks: two chunk buffers
+        for (int k = 0; k < 2; ++k) {
+            const StageCfg &sc = pl->st[k];
+            if (!sc.split) continue;
+            const int64_t Cst = (k == 0) ? pl->N2 : pl->N1;
+            const size_t e = (sc.sp_lgCc == ilog2_exact(Cst))
+                                 ? (size_t)(pl->N * pl->batch)
+                                 : 2 * (size_t)pl->batch * ((size_t)1 << (sc.lgLa + sc.lgLb + sc.sp_lgCc));
+            elems = std::max(elems, e);
+        }
+        cudaError_t ea = cudaMalloc(&pl->split_scratch, elems * pl->esize);
         if (ea != cudaSuccess) {
             paco_plan_destroy(pl);
             return fail(PACO_ERR_NOMEM, "split-stage scratch: %s", cudaGetErrorString(ea));
@@ -489,50 +507,65 @@ static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int m
     return PACO_OK;
 }
 
-// The two passes of a split stage: in -> scratch (pass A), scratch -> out (pass B).
+// The two passes of a split stage: in -> scratch (pass A), scratch -> out
+// (pass B), once for the whole stage or once per column chunk (two chunk
+// buffers in turn).
 static paco_status_t launch_split(const paco_plan *pl, const StageCfg &sc, int mode, const void *in, void *out,
                                   int dir, cudaStream_t stream)
 {
     const int64_t C = (mode == 1) ? pl->N2 : pl->N1;
     const int lgC = ilog2_exact(C);
-    for (int p = 0; p < 2; ++p) {
-        const int sub = (mode == 1) ? 1 + p : 3 + p;
-        StageArgs a;
-        memset(&a, 0, sizeof(a));
-        a.batch_stride = pl->N;
-        a.lgW = sc.sp_lgW[p];
-        a.lgK = 0;
-        a.mode = (sub == 1) ? 1 : 2;
-        a.rev_t = pl->t;
-        a.rev_bits = (sub == 3) ? sc.lgLa : sc.lgLb;     // sub 3: rows pi over La's digits (others: natural rows)
-        a.conj = (dir == 1);
-        a.N_mask = (unsigned)(pl->N - 1);
-        a.twN_lo = pl->twN_lo;
-        a.twN_hi = pl->twN_hi;
-        a.twN_lo_bits = pl->twN_lo_bits;
-        a.pad = (sub == 1) ? 1 : (1 << sc.sp_lgW[p]);
-        a.twL = sc.sp_tw[p];
-        a.C = (int)((sub == 1) ? (C << sc.lgLb) : (sub == 2) ? (C << sc.lgLa) : (sub == 3) ? C : (C << sc.lgLa));
-        a.out_ld = (int)((sub == 2) ? ((int64_t)1 << (sc.lgLa + sc.lgLb)) : C);
-        SplitArgs sa;
-        memset(&sa, 0, sizeof(sa));
-        sa.sub = sub;
-        sa.lgC = lgC;
-        sa.lgLa = sc.lgLa;
-        sa.lgLb = sc.lgLb;
-        sa.rev_bits_c = (mode == 1) ? lgC : 0;
-        sa.twS = (mode == 1) ? pl->twL1 : pl->twL2;
-        const void *src = (p == 0) ? in : pl->split_scratch;
-        void *dst = (p == 0) ? pl->split_scratch : out;
-        for (int64_t b0 = 0; b0 < pl->batch; b0 += 65535) {
-            const int64_t nb = (pl->batch - b0 < 65535) ? pl->batch - b0 : 65535;
-            StageArgs ab = a;
-            ab.in = (const char *)src + (size_t)(b0 * pl->N) * pl->esize;
-            ab.out = (char *)dst + (size_t)(b0 * pl->N) * pl->esize;
-            void *params[] = {&ab, &sa};
-            PACO_CUDA_TRY(cudaLaunchKernel(sc.sp_fn[p], dim3((unsigned)sc.sp_ntiles[p], (unsigned)nb, 1),
-                                           dim3((unsigned)sc.sp_threads[p], 1, 1), params, (size_t)sc.sp_smem[p],
-                                           stream));
+    const int lgCc = sc.sp_lgCc;
+    const bool chunked = lgCc < lgC;
+    const int64_t Cc = (int64_t)1 << lgCc;
+    const long long L = 1LL << (sc.lgLa + sc.lgLb);
+    const long long chunk_elems = L << lgCc;             // one transform's chunk of S
+    for (int64_t c_start = 0; c_start < C; c_start += Cc) {
+        void *scr = static_cast<char *>(pl->split_scratch) +
+                    (chunked ? (size_t)((c_start >> lgCc) & 1) * (size_t)(pl->batch * chunk_elems) * pl->esize : 0);
+        for (int p = 0; p < 2; ++p) {
+            const int sub = (mode == 1) ? 1 + p : 3 + p;
+            StageArgs a;
+            memset(&a, 0, sizeof(a));
+            a.lgW = sc.sp_lgW[p];
+            a.lgK = 0;
+            a.mode = (sub == 1) ? 1 : 2;
+            a.rev_t = pl->t;
+            a.rev_bits = (sub == 3) ? sc.lgLa : sc.lgLb;  // sub 3: rows pi over La's digits (others: natural rows)
+            a.conj = (dir == 1);
+            a.N_mask = (unsigned)(pl->N - 1);
+            a.twN_lo = pl->twN_lo;
+            a.twN_hi = pl->twN_hi;
+            a.twN_lo_bits = pl->twN_lo_bits;
+            a.pad = (sub == 1) ? 1 : (1 << sc.sp_lgW[p]);
+            a.twL = sc.sp_tw[p];
+            a.C = (int)((sub == 1) ? (C << sc.lgLb) : (sub == 2) ? (Cc << sc.lgLa) : (sub == 3) ? C : (Cc << sc.lgLa));
+            a.out_ld = (int)((sub == 2) ? L : C);
+            SplitArgs sa;
+            memset(&sa, 0, sizeof(sa));
+            sa.sub = sub;
+            sa.lgC = lgC;
+            sa.lgCc = lgCc;
+            sa.c_start = (int)c_start;
+            sa.lgLa = sc.lgLa;
+            sa.lgLb = sc.lgLb;
+            sa.rev_bits_c = (mode == 1) ? lgC : 0;
+            sa.twS = (mode == 1) ? pl->twL1 : pl->twL2;
+            sa.in_stride = (p == 0) ? pl->N : chunk_elems;
+            sa.out_stride = (p == 0) ? chunk_elems : pl->N;
+            if (!chunked) sa.in_stride = sa.out_stride = pl->N;
+            const void *src = (p == 0) ? in : scr;
+            void *dst = (p == 0) ? scr : out;
+            for (int64_t b0 = 0; b0 < pl->batch; b0 += 65535) {
+                const int64_t nb = (pl->batch - b0 < 65535) ? pl->batch - b0 : 65535;
+                StageArgs ab = a;
+                ab.in = (const char *)src + (size_t)(b0 * sa.in_stride) * pl->esize;
+                ab.out = (char *)dst + (size_t)(b0 * sa.out_stride) * pl->esize;
+                void *params[] = {&ab, &sa};
+                PACO_CUDA_TRY(cudaLaunchKernel(sc.sp_fn[p], dim3((unsigned)sc.sp_ntiles[p], (unsigned)nb, 1),
+                                               dim3((unsigned)sc.sp_threads[p], 1, 1), params, (size_t)sc.sp_smem[p],
+                                               stream));
+            }
         }
     }
     return PACO_OK;

@@ -208,13 +208,19 @@ struct ShardArgs {
 // epilogue), scratch S holding the intermediate.  sub: 1 Phase I pass A
 // (x -> S[j_b][c][k_a]), 2 Phase I pass B (S -> W[pi_m2(c)][k_a + La k_b]
 // with w_N^{-k1 c}), 3 Phase III pass A (W rows pi_m2(j) -> S[j_b][k_a][v]),
-// 4 Phase III pass B (S -> y[k_a + La k_b][v]).
+// 4 Phase III pass B (S -> y[k_a + La k_b][v]); c and v counted within the chunk
+// in S.
+// The passes may run on a chunk of the stage's columns, [c_start, c_start + Cc),
+// S then holding that chunk only (so that it can stay in L2 between them).
 struct SplitArgs {
     int sub;
-    int lgC;                // log2 of the stage's column count
+    int lgC;                // log2 of the stage's column count C
+    int lgCc;               // log2 of the chunk's column count (lgC: the whole stage)
+    int c_start;            // the chunk's first column
     int lgLa, lgLb;
     int rev_bits_c;         // sub 2: pi_m2 over log2 N2 bits
     const void *twS;        // w_L^{-r}, r < L (sub 1, 3)
+    long long in_stride, out_stride;   // elements between transforms of the batch (N, or the chunk's L Cc)
 };
 
 // Element-wise terms of a weighted power loss, taken by the stage kernels

@@ -25,6 +25,7 @@ struct StageCfg {
     // of length 2^lgLa, pass B of length 2^lgLb; SplitArgs in paco_common.cuh)
     int split = 0;
     int lgLa = 0, lgLb = 0;
+    int sp_lgCc = 0;                       // columns per chunk (log2); the whole stage when it equals log2 C
     int sp_lgW[2] = {0, 0}, sp_threads[2] = {0, 0}, sp_smem[2] = {0, 0}, sp_ntiles[2] = {0, 0};
     const void *sp_fn[2] = {nullptr, nullptr};
     void *sp_tw[2] = {nullptr, nullptr};   // w_{2^lgLa}^{-r} and w_{2^lgLb}^{-r}
@@ -51,6 +52,7 @@ struct paco_plan {
     int num_sms = 0;
     int form = 0;                  // tensor-core precision form (paco_tc.cuh), 0 = plain
     int req_ctas = 0;              // requested CTAs per SM of the stage kernels (0 = default)
+    int req_split = 0;             // paco_plan_opts_t.split
     unsigned dbg_spin_limit = 0;   // paco_debug_set_waits: poll limit of the bounded waits (0 = default)
     unsigned dbg_wait_bias = 0;    // paco_debug_set_waits: added to the dependency targets
     void *tc = nullptr;            // its fragment table

@@ -181,13 +181,14 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             // one pass of a split stage: the tile's twiddles (its columns share j_b, or c)
             if (sp->sub == 1 || sp->sub == 3) {
                 const C *twS = reinterpret_cast<const C *>(sp->twS);
-                const int jb = c0 >> sp->lgC;
+                const int jb = c0 >> sp->lgCc;
                 for (int r = tid; r < (1 << sp->lgLa); r += NT) E1[r] = ldg_cx(twS + r * jb);   // w_L^{-k_a j_b}
             } else if (sp->sub == 2) {
                 const C *nlo = reinterpret_cast<const C *>(args.twN_lo);
                 const C *nhi = reinterpret_cast<const C *>(args.twN_hi);
                 const unsigned lomask = (1u << args.twN_lo_bits) - 1u;
-                const unsigned cw = (unsigned)(c0 >> sp->lgLa), ka0 = (unsigned)(c0 & ((1 << sp->lgLa) - 1));
+                const unsigned cw = (unsigned)(sp->c_start + (c0 >> sp->lgLa));
+                const unsigned ka0 = (unsigned)(c0 & ((1 << sp->lgLa) - 1));
                 for (int e = tid; e < W; e += NT) {                                          // w_N^{-k_a c}
                     const unsigned r = ((ka0 + (unsigned)e) * cw) & args.N_mask;
                     E1[e] = cmul(ldg_cx(nlo + (r & lomask)), ldg_cx(nhi + (r >> args.twN_lo_bits)));
@@ -239,9 +240,12 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     [[maybe_unused]] long long cbase = 0;
     if constexpr (SPLIT) {
         cbase = c0;
-        if (sp->sub == 3)
-            cbase = ((long long)digit_reverse((unsigned)(c0 >> sp->lgC), sp->lgLb, args.rev_t) << (sp->lgLa + sp->lgC)) +
-                    (c0 & ((1 << sp->lgC) - 1));
+        const int jb = c0 >> sp->lgCc, cl = c0 & ((1 << sp->lgCc) - 1);
+        if (sp->sub == 1)                             // row j_a of x viewed [La][Lb C]: column j_b C + c
+            cbase = ((long long)jb << sp->lgC) + sp->c_start + cl;
+        else if (sp->sub == 3)                        // row pi(j_a) of W's row block pi(j_b)
+            cbase = ((long long)digit_reverse((unsigned)jb, sp->lgLb, args.rev_t) << (sp->lgLa + sp->lgC)) +
+                    sp->c_start + cl;
     }
 
     // ---- F1 pass 1: radix RA1 over j_hi, span RA2; operands straight from HBM
@@ -386,7 +390,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
 
     // ---- F2 pass 1: radix RB1 over j_lo, span RB2
     constexpr int NB1 = EPT / RB1;
-    C *gout = reinterpret_cast<C *>(args.out) + (SHARD ? boff_out : boff);
+    C *gout = reinterpret_cast<C *>(args.out) + ((SHARD || SPLIT) ? boff_out : boff);
 #pragma unroll
     for (int u = 0; u < NB1; ++u) {
         const int bfi = tid + NT * u;
@@ -496,20 +500,20 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             long long idx;
             if constexpr (SPLIT) {
                 const int cc = c0 + col;                      // the pass's view column
-                const int mC = (1 << sp->lgC) - 1;
+                const int mC = (1 << sp->lgCc) - 1;
                 if (sp->sub == 1) {                           // S[j_b][c][k_a], view column j_b C + c
                     y = cmul(y, E1[kk]);
                     idx = ((long long)cc << sp->lgLa) + kk;
                 } else if (sp->sub == 2) {                    // W[pi_m2(c)][k_a + La k_b], view column c La + k_a
                     y = cmul(y, cmul(E1[col], E2[kk]));
-                    const unsigned cw = (unsigned)(cc >> sp->lgLa);
+                    const unsigned cw = (unsigned)(sp->c_start + (cc >> sp->lgLa));
                     idx = (long long)digit_reverse(cw, sp->rev_bits_c, args.rev_t) * args.out_ld +
                           (cc & ((1 << sp->lgLa) - 1)) + ((long long)kk << sp->lgLa);
                 } else if (sp->sub == 3) {                    // S[j_b][k_a][v], view column j_b C + v
                     y = cmul(y, E1[kk]);
-                    idx = ((((long long)(c0 >> sp->lgC) << sp->lgLa) + kk) << sp->lgC) + (cc & mC);
+                    idx = ((((long long)(c0 >> sp->lgCc) << sp->lgLa) + kk) << sp->lgCc) + (cc & mC);
                 } else {                                      // y[k_a + La k_b][v], view column k_a C + v
-                    idx = (long long)((cc >> sp->lgC) + (kk << sp->lgLa)) * args.out_ld + (cc & mC);
+                    idx = (long long)((cc >> sp->lgCc) + (kk << sp->lgLa)) * args.out_ld + sp->c_start + (cc & mC);
                 }
             } else if (mode == 1) {
                 y = cmul(y, cmul(E1[(col << (ilog2c<A>::value - lgK)) + al], E2[(khi << lgW) + col]));
@@ -583,7 +587,8 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel_split(const Stage
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     stage_tile<R, A, B, -1, 0, 0, false, TC_NONE, false, false, true>(
-        args, (int)blockIdx.x, (long long)blockIdx.y * args.batch_stride, 0, smem_raw, nullptr, nullptr, 0, &sp);
+        args, (int)blockIdx.x, (long long)blockIdx.y * sp.in_stride, 0, smem_raw, nullptr, nullptr,
+        (long long)blockIdx.y * sp.out_stride, &sp);
 }
 
 // The generic stage with the element-wise terms of a weighted power loss

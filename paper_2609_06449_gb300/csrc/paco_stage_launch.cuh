@@ -46,7 +46,7 @@ const void *stage_kernel_fn_shard(int lgL, int minb)
 #undef PACO_SHARD_CASE
 }
 
-// One pass of a split stage, length 2^lgL (complex64).
+// One pass of a split stage, length 2^lgL (complex64, 2^5..2^8).
 template <typename R>
 const void *stage_kernel_fn_split(int lgL, int minb)
 {
@@ -57,7 +57,7 @@ const void *stage_kernel_fn_split(int lgL, int minb)
         return reinterpret_cast<const void *>(&paco_stage_kernel_split<R, A_, B_, 1>);               \
     }
     switch (lgL) {
-        PACO_SPLIT_CASE(5) PACO_SPLIT_CASE(6) PACO_SPLIT_CASE(7)
+        PACO_SPLIT_CASE(5) PACO_SPLIT_CASE(6) PACO_SPLIT_CASE(7) PACO_SPLIT_CASE(8)
     default: return nullptr;
     }
 #undef PACO_SPLIT_CASE

@@ -173,6 +173,29 @@ def test_split_stages_against_oracle(N1, N2, b, batch, split, d):
     assert rel_l2(got, ref) <= 5e-7 * math.log2(N), (N1, N2, b)
 
 
+@pytest.mark.parametrize("N1,N2,b,batch", [(16384, 2048, 2, 2), (16384, 4096, 4, 1), (4096, 16384, 4, 2),
+                                            (16384, 512, 2, 1), (16384, 16384, 4, 1)])
+@pytest.mark.parametrize("d", [-1, 1])
+def test_split_2p14_in_column_chunks(N1, N2, b, batch, d):
+    """split=1: 2^14 stages as two passes per chunk of 256 columns (the
+    intermediate in two chunk buffers that alternate) -- every transform
+    element by element against the oracle, both directions, three times (a
+    race between the chunks would show as a run that differs)."""
+    N = N1 * N2
+    plan = paco.Plan(N1, N2, b, batch, paco.C64, split=1)
+    want = tuple(int(L >= 4096) for L in (N1, N2))
+    assert tuple(plan.info.stage_split) == want
+    x = uniform(batch * N, N1 + N2 + 7 * b, np.complex64).reshape(batch, N)
+    ref = oracle.fft(x.astype(np.complex128), dir=d, threads=0)
+    first = None
+    for _ in range(3):
+        got = run(plan, x, d)
+        assert rel_l2(got, ref) <= 5e-7 * math.log2(N), (N1, N2, b)
+        if first is None:
+            first = got
+        assert np.array_equal(got, first)
+
+
 def test_closed_forms_on_gpu():
     """delta -> constant; single tone -> N delta; Parseval."""
     N1 = N2 = 256
