@@ -90,11 +90,10 @@ typedef struct {
     int cluster;         /* CTAs per cluster (1, 2, 4, 8); 0 = default */
     int ctas_per_sm;     /* resident CTAs per SM the stage kernels are compiled
                             for (1 or 2; complex64 stage kernels only); 0 = default */
-    int split;           /* complex64 stages of 2^12..2^14 as two passes through
-                            scratch (paco_plan_info.stage_split): 0 = default (2^12,
-                            2^13; 2^14 keeps the L2 panel pipeline), 1 = wherever
-                            possible (2^14 in column chunks that keep the
-                            intermediate in L2), -1 = never */
+    int split;           /* complex64 stages of 2^12..2^14 as two passes through an
+                            N * batch scratch (paco_plan_info.stage_split): 0 =
+                            default (2^12, 2^13; 2^14 keeps the L2 panel pipeline),
+                            1 = 2^14 as well, -1 = never */
 } paco_plan_opts_t;
 
 /* Read-only description of a plan (paco_plan_info). */
@@ -234,11 +233,13 @@ paco_status_t paco_probe_tc05_dft128(const void *x, void *y, int64_t batch, int6
 
 /*
  * paco_execute_weighted_power -- paco_execute plus the weighted power of the
- * result, for a spectral loss: out = y = F^dir x as paco_execute computes it,
- * and *loss = sum over the whole batch of w[n] |y[n]|^2, accumulated by the
+ * result, for a spectral loss: y = F^dir x as paco_execute computes it, and
+ * *loss = sum over the whole batch of w[n] |y[n]|^2, accumulated by the
  * Phase III kernel as it stores y (the sum is not a separate pass; *loss is
  * set to 0 on `stream` first, then added to atomically in FP64: its rounding
- * order varies between runs).  w: device, batch*N floats in the layout of y;
+ * order varies between runs).  out_weighted = 0 stores y in `out`; 1 stores
+ * w ⊙ y instead (what the loss's backward needs, at no extra cost: the
+ * kernel already holds w[n]).  w: device, batch*N floats in the layout of y;
  * loss: device, one double, 8-byte aligned.  The paper's transform is
  * unchanged (Theorem 3); the loss is an epilogue of the last stage.  Plans
  * with a 2^14 complex64 factor (panel stages) and uneven-batch plans return
@@ -246,17 +247,18 @@ paco_status_t paco_probe_tc05_dft128(const void *x, void *y, int64_t batch, int6
  * here.  Asynchronous on `stream`.
  */
 paco_status_t paco_execute_weighted_power(paco_plan_t *plan, const void *in, void *out, const float *w,
-                                          double *loss, int dir, paco_stream_t stream);
+                                          double *loss, int out_weighted, int dir, paco_stream_t stream);
 
 /*
  * paco_execute_weighted_input -- out = F^dir (s * w ⊙ in) with the
  * element-wise product applied as Phase I loads its input (no separate
- * pass): s = mult * (*scale), or mult when scale is NULL.  w: device,
- * batch*N floats in the layout of `in`; scale: device double or NULL.  With
- * dir = +1, w the loss weights, in = y, mult = 2 and scale the incoming
- * gradient of the loss of paco_execute_weighted_power, out is that loss's
- * gradient with respect to x (F^H (2 g w ⊙ F x), the conjugate transform
- * being F^H).  Same plans and errors as paco_execute_weighted_power.
+ * pass): s = mult * (*scale), or mult when scale is NULL; w = NULL applies
+ * the scalar s alone.  w: device, batch*N floats in the layout of `in`;
+ * scale: device double or NULL.  With dir = +1, in = w ⊙ y (the output of
+ * paco_execute_weighted_power with out_weighted = 1), w = NULL, mult = 2 and
+ * scale the incoming gradient g of that loss, out is the loss's gradient
+ * with respect to x, F^H (2 g w ⊙ F x) (the conjugate transform being F^H).
+ * Same plans and errors as paco_execute_weighted_power.
  */
 paco_status_t paco_execute_weighted_input(paco_plan_t *plan, const void *in, void *out, const float *w,
                                           const double *scale, float mult, int dir, paco_stream_t stream);

@@ -148,7 +148,7 @@ def _load():
     L.paco_execute_noalloc.restype = i32
     L.paco_probe_fp64_peak.argtypes = [i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float), vp]
     L.paco_probe_fp64_peak.restype = i32
-    L.paco_execute_weighted_power.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+    L.paco_execute_weighted_power.argtypes = [vp, vp, vp, vp, vp, i32, i32, vp]
     L.paco_execute_weighted_power.restype = i32
     L.paco_execute_weighted_input.argtypes = [vp, vp, vp, vp, vp, ctypes.c_float, i32, vp]
     L.paco_execute_weighted_input.restype = i32
@@ -263,14 +263,16 @@ class Plan:
     def execute(self, x, out, dir: int = -1, stream=None) -> None:
         _check(lib.paco_execute(self._h, _ptr(x), _ptr(out), int(dir), _stream(stream)))
 
-    def execute_weighted_power(self, x, out, w, loss, dir: int = -1, stream=None) -> None:
-        """out = F^dir x and loss[0] = sum(w |out|^2) (float32 w, float64 loss, device)."""
-        _check(lib.paco_execute_weighted_power(self._h, _ptr(x), _ptr(out), _ptr(w), _ptr(loss), int(dir),
-                                               _stream(stream)))
+    def execute_weighted_power(self, x, out, w, loss, dir: int = -1, stream=None, out_weighted: bool = False) -> None:
+        """y = F^dir x, loss[0] = sum(w |y|^2) (float32 w, float64 loss, device);
+        out = y, or w * y with ``out_weighted``."""
+        _check(lib.paco_execute_weighted_power(self._h, _ptr(x), _ptr(out), _ptr(w), _ptr(loss),
+                                               1 if out_weighted else 0, int(dir), _stream(stream)))
 
     def execute_weighted_input(self, x, out, w, scale=None, mult: float = 1.0, dir: int = -1,
                                stream=None) -> None:
-        """out = F^dir (mult * scale[0] * w * x); scale a float64 device scalar or None."""
+        """out = F^dir (mult * scale[0] * w * x); scale a float64 device scalar or
+        None, w a float32 device tensor or None (the scalar alone)."""
         _check(lib.paco_execute_weighted_input(self._h, _ptr(x), _ptr(out), _ptr(w), _ptr(scale),
                                                float(mult), int(dir), _stream(stream)))
 
@@ -426,10 +428,10 @@ try:
     class PacoWeightedPowerLoss(_torch.autograd.Function):
         """loss = sum(w |F x|^2) over the whole batch (float64 scalar), F the
         paper's forward transform.  Forward: the two stage kernels, the loss
-        summed by the Phase III kernel as it stores y = F x.  Backward:
-        grad_x = F^H (2 g w ⊙ y), the product applied as the conjugate
-        transform's Phase I loads its input.  w (float32, the shape of x) is
-        treated as a constant."""
+        summed by the Phase III kernel, which stores u = w ⊙ F x (y itself is
+        not returned).  Backward: grad_x = F^H (2 g u), the scalar 2 g applied
+        as the conjugate transform's Phase I loads its input.  w (float32, the
+        shape of x) is treated as a constant."""
 
         @staticmethod
         def forward(ctx, x, w, N1, N2, b, p=0):
@@ -444,21 +446,21 @@ try:
             stream = int(_torch.cuda.current_stream(xc.device).cuda_stream)
             with _torch.cuda.device(xc.device.index):
                 pl = get_plan(int(N1), int(N2), int(b), xc.numel() // N, C64, int(p), xc.device.index, stream)
-                pl.execute_weighted_power(xc, y, wc, loss, -1, stream)
-            ctx.save_for_backward(y, wc)
+                pl.execute_weighted_power(xc, y, wc, loss, -1, stream, out_weighted=True)
+            ctx.save_for_backward(y)
             ctx.cfg = (int(N1), int(N2), int(b), int(p), stream)
             return loss
 
         @staticmethod
         def backward(ctx, g):
-            y, wc = ctx.saved_tensors
+            (y,) = ctx.saved_tensors
             N1, N2, b, p, _ = ctx.cfg
             g = g.to(_torch.float64).contiguous()
             gx = _torch.empty_like(y)
             stream = int(_torch.cuda.current_stream(y.device).cuda_stream)
             with _torch.cuda.device(y.device.index):
                 pl = get_plan(N1, N2, b, y.numel() // (N1 * N2), C64, p, y.device.index, stream)
-                pl.execute_weighted_input(y, gx, wc, g, 2.0, +1, stream)
+                pl.execute_weighted_input(y, gx, None, g, 2.0, +1, stream)
             return gx, None, None, None, None, None
 
     def weighted_power_loss(x, w, N1: int, N2: int, b: int, p: int = 0):

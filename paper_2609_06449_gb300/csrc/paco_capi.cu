@@ -28,6 +28,7 @@ const void *stage_kernel_fn_f64(int lgL, int minb);
 const void *stage_kernel_fn_special_f32(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_special_f64(int lgL, int lgW, int lgK, int mode);
 const void *stage_kernel_fn_terms_f32(int lgL, int minb);
+const void *stage_kernel_fn_scale_f32(int lgL, int minb);
 const void *stage_kernel_fn_shard_f32(int lgL, int minb);
 const void *stage_kernel_fn_split_f32(int lgL, int minb);
 } // namespace paco
@@ -158,14 +159,12 @@ static paco_status_t setup_split(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
     const int lgLb = lgL - lgLa;
     if (lgLb % pl->t || lgLb < 5 || lgLa > 8) return PACO_OK;
     const int lgC = ilog2_exact(C);
-    // 2^14: column chunks of 256, whose intermediate (32 MiB a transform) stays in L2
-    const int lgCc = (lgL == 14 && lgC > 8) ? 8 : lgC;
     for (int p = 0; p < 2; ++p) {
         const int lgLs = p == 0 ? lgLa : lgLb;
-        const int64_t Cv = ((int64_t)1 << ((p == 0 ? lgLb : lgLa) + lgCc));   // the pass's view columns
+        const int64_t Cv = ((int64_t)1 << (p == 0 ? lgLb : lgLa)) * C;   // the pass's view columns
         int lgW = 0, lgK = 0;
         choose_tile(pl, lgLs, Cv, 0, 0, 2, &lgW, &lgK);
-        if (lgW > lgCc) lgW = lgCc;                      // a tile stays inside one column block
+        if (lgW > lgC) lgW = lgC;                        // a tile stays inside one column block
         if (mode == 1 && p == 1 && lgW > lgLa) lgW = lgLa;
         const int As = 1 << ((lgLs + 1) / 2), Bs = 1 << (lgLs / 2), W = 1 << lgW;
         const bool fits = lgK == 0 && ((p == 0 && (1 << lgLa) <= (As + Bs) * W) ||
@@ -187,7 +186,6 @@ static paco_status_t setup_split(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         return st;
     sc->lgLa = lgLa;
     sc->lgLb = lgLb;
-    sc->sp_lgCc = lgCc;
     sc->split = 1;
     return PACO_OK;
 }
@@ -267,9 +265,9 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         // the weighted-loss variant of the generic kernel (runtime tile width and
         // cluster size, so it also stands in for a specialised kernel)
         sc->fn_terms = stage_kernel_fn_terms_f32(lgL, (two || !generic) ? 2 : 1);
-        if (sc->fn_terms)
-            PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn_terms, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               227 * 1024));
+        sc->fn_scale = stage_kernel_fn_scale_f32(lgL, (two || !generic) ? 2 : 1);
+        for (const void *f : {sc->fn_terms, sc->fn_scale})
+            if (f) PACO_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     }
     return PACO_OK;
 }
@@ -373,17 +371,7 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
         pl->ctr_words = words;
     }
     if ((pl->st[0].split || pl->st[1].split) && pl->batch > 0) {
-        size_t elems = 0;                                // whole stages: N a transform; chunks: two chunk buffers
-        for (int k = 0; k < 2; ++k) {
-            const StageCfg &sc = pl->st[k];
-            if (!sc.split) continue;
-            const int64_t Cst = (k == 0) ? pl->N2 : pl->N1;
-            const size_t e = (sc.sp_lgCc == ilog2_exact(Cst))
-                                 ? (size_t)(pl->N * pl->batch)
-                                 : 2 * (size_t)pl->batch * ((size_t)1 << (sc.lgLa + sc.lgLb + sc.sp_lgCc));
-            elems = std::max(elems, e);
-        }
-        cudaError_t ea = cudaMalloc(&pl->split_scratch, elems * pl->esize);
+        cudaError_t ea = cudaMalloc(&pl->split_scratch, (size_t)(pl->N * pl->batch) * pl->esize);
         if (ea != cudaSuccess) {
             paco_plan_destroy(pl);
             return fail(PACO_ERR_NOMEM, "split-stage scratch: %s", cudaGetErrorString(ea));
@@ -507,65 +495,50 @@ static paco_status_t launch_panel(const paco_plan *pl, const StageCfg &sc, int m
     return PACO_OK;
 }
 
-// The two passes of a split stage: in -> scratch (pass A), scratch -> out
-// (pass B), once for the whole stage or once per column chunk (two chunk
-// buffers in turn).
+// The two passes of a split stage: in -> scratch (pass A), scratch -> out (pass B).
 static paco_status_t launch_split(const paco_plan *pl, const StageCfg &sc, int mode, const void *in, void *out,
                                   int dir, cudaStream_t stream)
 {
     const int64_t C = (mode == 1) ? pl->N2 : pl->N1;
     const int lgC = ilog2_exact(C);
-    const int lgCc = sc.sp_lgCc;
-    const bool chunked = lgCc < lgC;
-    const int64_t Cc = (int64_t)1 << lgCc;
-    const long long L = 1LL << (sc.lgLa + sc.lgLb);
-    const long long chunk_elems = L << lgCc;             // one transform's chunk of S
-    for (int64_t c_start = 0; c_start < C; c_start += Cc) {
-        void *scr = static_cast<char *>(pl->split_scratch) +
-                    (chunked ? (size_t)((c_start >> lgCc) & 1) * (size_t)(pl->batch * chunk_elems) * pl->esize : 0);
-        for (int p = 0; p < 2; ++p) {
-            const int sub = (mode == 1) ? 1 + p : 3 + p;
-            StageArgs a;
-            memset(&a, 0, sizeof(a));
-            a.lgW = sc.sp_lgW[p];
-            a.lgK = 0;
-            a.mode = (sub == 1) ? 1 : 2;
-            a.rev_t = pl->t;
-            a.rev_bits = (sub == 3) ? sc.lgLa : sc.lgLb;  // sub 3: rows pi over La's digits (others: natural rows)
-            a.conj = (dir == 1);
-            a.N_mask = (unsigned)(pl->N - 1);
-            a.twN_lo = pl->twN_lo;
-            a.twN_hi = pl->twN_hi;
-            a.twN_lo_bits = pl->twN_lo_bits;
-            a.pad = (sub == 1) ? 1 : (1 << sc.sp_lgW[p]);
-            a.twL = sc.sp_tw[p];
-            a.C = (int)((sub == 1) ? (C << sc.lgLb) : (sub == 2) ? (Cc << sc.lgLa) : (sub == 3) ? C : (Cc << sc.lgLa));
-            a.out_ld = (int)((sub == 2) ? L : C);
-            SplitArgs sa;
-            memset(&sa, 0, sizeof(sa));
-            sa.sub = sub;
-            sa.lgC = lgC;
-            sa.lgCc = lgCc;
-            sa.c_start = (int)c_start;
-            sa.lgLa = sc.lgLa;
-            sa.lgLb = sc.lgLb;
-            sa.rev_bits_c = (mode == 1) ? lgC : 0;
-            sa.twS = (mode == 1) ? pl->twL1 : pl->twL2;
-            sa.in_stride = (p == 0) ? pl->N : chunk_elems;
-            sa.out_stride = (p == 0) ? chunk_elems : pl->N;
-            if (!chunked) sa.in_stride = sa.out_stride = pl->N;
-            const void *src = (p == 0) ? in : scr;
-            void *dst = (p == 0) ? scr : out;
-            for (int64_t b0 = 0; b0 < pl->batch; b0 += 65535) {
-                const int64_t nb = (pl->batch - b0 < 65535) ? pl->batch - b0 : 65535;
-                StageArgs ab = a;
-                ab.in = (const char *)src + (size_t)(b0 * sa.in_stride) * pl->esize;
-                ab.out = (char *)dst + (size_t)(b0 * sa.out_stride) * pl->esize;
-                void *params[] = {&ab, &sa};
-                PACO_CUDA_TRY(cudaLaunchKernel(sc.sp_fn[p], dim3((unsigned)sc.sp_ntiles[p], (unsigned)nb, 1),
-                                               dim3((unsigned)sc.sp_threads[p], 1, 1), params, (size_t)sc.sp_smem[p],
-                                               stream));
-            }
+    for (int p = 0; p < 2; ++p) {
+        const int sub = (mode == 1) ? 1 + p : 3 + p;
+        StageArgs a;
+        memset(&a, 0, sizeof(a));
+        a.batch_stride = pl->N;
+        a.lgW = sc.sp_lgW[p];
+        a.lgK = 0;
+        a.mode = (sub == 1) ? 1 : 2;
+        a.rev_t = pl->t;
+        a.rev_bits = (sub == 3) ? sc.lgLa : sc.lgLb;     // sub 3: rows pi over La's digits (others: natural rows)
+        a.conj = (dir == 1);
+        a.N_mask = (unsigned)(pl->N - 1);
+        a.twN_lo = pl->twN_lo;
+        a.twN_hi = pl->twN_hi;
+        a.twN_lo_bits = pl->twN_lo_bits;
+        a.pad = (sub == 1) ? 1 : (1 << sc.sp_lgW[p]);
+        a.twL = sc.sp_tw[p];
+        a.C = (int)((sub == 1) ? (C << sc.lgLb) : (sub == 2) ? (C << sc.lgLa) : (sub == 3) ? C : (C << sc.lgLa));
+        a.out_ld = (int)((sub == 2) ? ((int64_t)1 << (sc.lgLa + sc.lgLb)) : C);
+        SplitArgs sa;
+        memset(&sa, 0, sizeof(sa));
+        sa.sub = sub;
+        sa.lgC = lgC;
+        sa.lgLa = sc.lgLa;
+        sa.lgLb = sc.lgLb;
+        sa.rev_bits_c = (mode == 1) ? lgC : 0;
+        sa.twS = (mode == 1) ? pl->twL1 : pl->twL2;
+        const void *src = (p == 0) ? in : pl->split_scratch;
+        void *dst = (p == 0) ? pl->split_scratch : out;
+        for (int64_t b0 = 0; b0 < pl->batch; b0 += 65535) {
+            const int64_t nb = (pl->batch - b0 < 65535) ? pl->batch - b0 : 65535;
+            StageArgs ab = a;
+            ab.in = (const char *)src + (size_t)(b0 * pl->N) * pl->esize;
+            ab.out = (char *)dst + (size_t)(b0 * pl->N) * pl->esize;
+            void *params[] = {&ab, &sa};
+            PACO_CUDA_TRY(cudaLaunchKernel(sc.sp_fn[p], dim3((unsigned)sc.sp_ntiles[p], (unsigned)nb, 1),
+                                           dim3((unsigned)sc.sp_threads[p], 1, 1), params, (size_t)sc.sp_smem[p],
+                                           stream));
         }
     }
     return PACO_OK;
@@ -636,7 +609,8 @@ static paco_status_t launch_stage(const paco_plan *pl, const StageCfg &sc, int m
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         void *params[] = {&ab, &tb};
-        PACO_CUDA_TRY(cudaLaunchKernelExC(&cfg, terms ? sc.fn_terms : sc.fn, params));
+        const void *fn = !terms ? sc.fn : (terms->ld_on && !terms->ld_w && !terms->st_w) ? sc.fn_scale : sc.fn_terms;
+        PACO_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, params));
     }
     return PACO_OK;
 }
@@ -798,7 +772,7 @@ static paco_status_t check_weighted(const paco_plan *pl, const char *fn)
 }
 
 extern "C" paco_status_t paco_execute_weighted_power(paco_plan_t *pl, const void *in, void *out, const float *w,
-                                                     double *loss, int dir, paco_stream_t stream)
+                                                     double *loss, int out_weighted, int dir, paco_stream_t stream)
 {
     paco_status_t st = check_exec(pl, in, out, dir, false);
     if (st != PACO_OK) return st;
@@ -814,6 +788,7 @@ extern "C" paco_status_t paco_execute_weighted_power(paco_plan_t *pl, const void
     memset(&t, 0, sizeof(t));
     t.st_w = w;
     t.st_loss = loss;
+    t.st_weighted = out_weighted ? 1 : 0;
     if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s)) != PACO_OK) return st;
     return launch_stage(pl, pl->st[1], 2, out, out, dir, s, &t);
 }
@@ -825,7 +800,6 @@ extern "C" paco_status_t paco_execute_weighted_input(paco_plan_t *pl, const void
     paco_status_t st = check_exec(pl, in, out, dir, false);
     if (st != PACO_OK) return st;
     if ((st = check_weighted(pl, "paco_execute_weighted_input")) != PACO_OK) return st;
-    if (!w) return fail(PACO_ERR_INVALID_ARG, "paco_execute_weighted_input: w required");
     if (((uintptr_t)w & 3u) || ((uintptr_t)scale & 7u))
         return fail(PACO_ERR_INVALID_ARG, "paco_execute_weighted_input: w must be 4-byte, scale 8-byte aligned");
     if (pl->batch == 0) return PACO_OK;
@@ -836,6 +810,7 @@ extern "C" paco_status_t paco_execute_weighted_input(paco_plan_t *pl, const void
     t.ld_w = w;
     t.ld_scale = scale;
     t.ld_mult = mult;
+    t.ld_on = 1;
     if ((st = launch_stage(pl, pl->st[0], 1, in, out, dir, s, &t)) != PACO_OK) return st;
     return launch_stage(pl, pl->st[1], 2, out, out, dir, s);
 }

@@ -208,29 +208,25 @@ struct ShardArgs {
 // epilogue), scratch S holding the intermediate.  sub: 1 Phase I pass A
 // (x -> S[j_b][c][k_a]), 2 Phase I pass B (S -> W[pi_m2(c)][k_a + La k_b]
 // with w_N^{-k1 c}), 3 Phase III pass A (W rows pi_m2(j) -> S[j_b][k_a][v]),
-// 4 Phase III pass B (S -> y[k_a + La k_b][v]); c and v counted within the chunk
-// in S.
-// The passes may run on a chunk of the stage's columns, [c_start, c_start + Cc),
-// S then holding that chunk only (so that it can stay in L2 between them).
+// 4 Phase III pass B (S -> y[k_a + La k_b][v]).
 struct SplitArgs {
     int sub;
-    int lgC;                // log2 of the stage's column count C
-    int lgCc;               // log2 of the chunk's column count (lgC: the whole stage)
-    int c_start;            // the chunk's first column
+    int lgC;                // log2 of the stage's column count
     int lgLa, lgLb;
     int rev_bits_c;         // sub 2: pi_m2 over log2 N2 bits
     const void *twS;        // w_L^{-r}, r < L (sub 1, 3)
-    long long in_stride, out_stride;   // elements between transforms of the batch (N, or the chunk's L Cc)
 };
 
 // Element-wise terms of a weighted power loss, taken by the stage kernels
 // built with them (paco_stage_kernel_terms); nullptr switches a term off.
 struct StageTerms {
     const float *ld_w;      // mode 1: element n of the input is read as
-    const double *ld_scale; //   ld_mult * (*ld_scale or 1) * ld_w[n] * in[n]
+    const double *ld_scale; //   ld_mult * (*ld_scale or 1) * (ld_w[n] or 1) * in[n]
     float ld_mult;
-    const float *st_w;      // mode 2: *st_loss += sum over n of st_w[n] |out[n]|^2
+    int ld_on;              //   (1: that factor is applied)
+    const float *st_w;      // mode 2: *st_loss += sum over n of st_w[n] |out[n]|^2,
     double *st_loss;
+    int st_weighted;        //   and (1) out[n] = st_w[n] * y[n] is stored in place of y[n]
 };
 
 } // namespace paco

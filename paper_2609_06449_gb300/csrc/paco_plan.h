@@ -19,13 +19,13 @@ struct StageCfg {
     int ntiles = 0;   // column tiles per transform
     const void *fn = nullptr;
     const void *fn_terms = nullptr;   // the same stage with the weighted-loss terms (complex64), or nullptr
+    const void *fn_scale = nullptr;   // ... with the scalar factor on Phase I's loads alone
     int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
     int P = 0;        // panel width (columns)
     // split = 1: the stage runs as two passes through the plan's scratch (pass A
     // of length 2^lgLa, pass B of length 2^lgLb; SplitArgs in paco_common.cuh)
     int split = 0;
     int lgLa = 0, lgLb = 0;
-    int sp_lgCc = 0;                       // columns per chunk (log2); the whole stage when it equals log2 C
     int sp_lgW[2] = {0, 0}, sp_threads[2] = {0, 0}, sp_smem[2] = {0, 0}, sp_ntiles[2] = {0, 0};
     const void *sp_fn[2] = {nullptr, nullptr};
     void *sp_tw[2] = {nullptr, nullptr};   // w_{2^lgLa}^{-r} and w_{2^lgLb}^{-r}

@@ -108,12 +108,14 @@ __host__ __device__ inline int stage_smem_elems(int A, int B, int K, int W, int 
 // FORM != TC_NONE computes the radix-16 passes (F1 and F2 pass 1 when the
 // radix is 16) as tensor-core contractions (paco_tc.cuh); its fragment table
 // and per-warp staging follow the stage's shared memory.
-// TERMS: the weighted-loss terms (StageTerms) are compiled in.  SHARD: the
+// TERMS: the weighted-loss terms (StageTerms) are compiled in (1: all of
+// them; 2: only the scalar factor on Phase I's loads).  SPLIT = 1: one pass of
+// a split stage (SplitArgs).  SHARD: the
 // sharded form's addresses (ShardArgs): Phase I on a local input slab with
 // global twiddle columns, stored into the G send blocks; Phase III reading
 // the received blocks; the output offset of the transform is boff_out.
-template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE, bool TERMS = false,
-          bool SHARD = false, bool SPLIT = false>
+template <typename R, int A, int B, int LGWC, int LGKC, int MC, bool LDCG, int FORM = TC_NONE, int TERMS = 0,
+          bool SHARD = false, int SPLIT = 0>
 __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long long boff, int rank,
                                            unsigned char *smem_raw, const StageTerms *terms = nullptr,
                                            const ShardArgs *sh = nullptr, long long boff_out = 0,
@@ -177,18 +179,28 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
         for (int r = tid; r < B; r += NT) twB[r] = ldg_cx(twL + r * A);
         for (int r = tid; r < SL; r += NT) tlo[r] = ldg_cx(twL + r);
         for (int r = tid; r < SH; r += NT) thi[r] = ldg_cx(twL + r * SL);
-        if constexpr (SPLIT) {
+        if constexpr (TERMS == 2) {
+            // the scalar factor of Phase I's input, folded into the twiddle
+            // every element takes after F1 (the DFT is linear): no per-element work
+            if (mode == 1 && terms->ld_on) {
+                const R f = R(terms->ld_mult) * (terms->ld_scale ? R(__ldg(terms->ld_scale)) : R(1));
+                for (int r = tid; r < SH; r += NT) {
+                    thi[r].x *= f;
+                    thi[r].y *= f;
+                }
+            }
+        }
+        if constexpr (SPLIT != 0) {
             // one pass of a split stage: the tile's twiddles (its columns share j_b, or c)
             if (sp->sub == 1 || sp->sub == 3) {
                 const C *twS = reinterpret_cast<const C *>(sp->twS);
-                const int jb = c0 >> sp->lgCc;
+                const int jb = c0 >> sp->lgC;
                 for (int r = tid; r < (1 << sp->lgLa); r += NT) E1[r] = ldg_cx(twS + r * jb);   // w_L^{-k_a j_b}
             } else if (sp->sub == 2) {
                 const C *nlo = reinterpret_cast<const C *>(args.twN_lo);
                 const C *nhi = reinterpret_cast<const C *>(args.twN_hi);
                 const unsigned lomask = (1u << args.twN_lo_bits) - 1u;
-                const unsigned cw = (unsigned)(sp->c_start + (c0 >> sp->lgLa));
-                const unsigned ka0 = (unsigned)(c0 & ((1 << sp->lgLa) - 1));
+                const unsigned cw = (unsigned)(c0 >> sp->lgLa), ka0 = (unsigned)(c0 & ((1 << sp->lgLa) - 1));
                 for (int e = tid; e < W; e += NT) {                                          // w_N^{-k_a c}
                     const unsigned r = ((ka0 + (unsigned)e) * cw) & args.N_mask;
                     E1[e] = cmul(ldg_cx(nlo + (r & lomask)), ldg_cx(nhi + (r >> args.twN_lo_bits)));
@@ -231,21 +243,18 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     // weighted input (mode 1): one real factor per element
     bool ldw = false;
     R lds = R(1);
-    if constexpr (TERMS) {
-        ldw = (mode == 1) && terms->ld_w != nullptr;
+    if constexpr (TERMS == 1) {
+        ldw = (mode == 1) && terms->ld_on;
         if (ldw) lds = R(terms->ld_mult) * (terms->ld_scale ? R(__ldg(terms->ld_scale)) : R(1));
     }
 
     // split pass A of Phase III: the tile's column block j_b lies in W's row block pi(j_b)
     [[maybe_unused]] long long cbase = 0;
-    if constexpr (SPLIT) {
+    if constexpr (SPLIT != 0) {
         cbase = c0;
-        const int jb = c0 >> sp->lgCc, cl = c0 & ((1 << sp->lgCc) - 1);
-        if (sp->sub == 1)                             // row j_a of x viewed [La][Lb C]: column j_b C + c
-            cbase = ((long long)jb << sp->lgC) + sp->c_start + cl;
-        else if (sp->sub == 3)                        // row pi(j_a) of W's row block pi(j_b)
-            cbase = ((long long)digit_reverse((unsigned)jb, sp->lgLb, args.rev_t) << (sp->lgLa + sp->lgC)) +
-                    sp->c_start + cl;
+        if (sp->sub == 3)
+            cbase = ((long long)digit_reverse((unsigned)(c0 >> sp->lgC), sp->lgLb, args.rev_t) << (sp->lgLa + sp->lgC)) +
+                    (c0 & ((1 << sp->lgC) - 1));
     }
 
     // ---- F1 pass 1: radix RA1 over j_hi, span RA2; operands straight from HBM
@@ -269,15 +278,16 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                               digit_reverse((unsigned)j & ((1u << sh->lgCl) - 1u), args.rev_bits, args.rev_t);
                 }
                 C x;
-                if constexpr (SPLIT) {
+                if constexpr (SPLIT != 0) {
                     if (sp->sub != 3) row = (unsigned)j;               // natural rows (sub 3: pi over La's digits)
                     x = ldg_cx(gin + (long long)row * args.C + cbase + col);
                 } else {
                     x = LDCG ? ldcg_cx(gin + (long long)row * args.C + c0 + col)
                              : ldg_cx(gin + (long long)row * args.C + c0 + col);
                 }
-                if constexpr (TERMS) if (ldw) {
-                    const R f = lds * R(__ldg(terms->ld_w + boff + (long long)row * args.C + c0 + col));
+                if constexpr (TERMS == 1) if (ldw) {
+                    R f = lds;
+                    if (terms->ld_w) f *= R(__ldg(terms->ld_w + boff + (long long)row * args.C + c0 + col));
                     x.x *= f;
                     x.y *= f;
                 }
@@ -390,7 +400,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
 
     // ---- F2 pass 1: radix RB1 over j_lo, span RB2
     constexpr int NB1 = EPT / RB1;
-    C *gout = reinterpret_cast<C *>(args.out) + ((SHARD || SPLIT) ? boff_out : boff);
+    C *gout = reinterpret_cast<C *>(args.out) + (SHARD ? boff_out : boff);
 #pragma unroll
     for (int u = 0; u < NB1; ++u) {
         const int bfi = tid + NT * u;
@@ -450,7 +460,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
     constexpr int RL = (RB2 > 1) ? RB2 : RB1;    // radix of the last pass
     constexpr int NBL = EPT / RL;
     bool stw = false;                             // weighted power of the output
-    if constexpr (TERMS) stw = (mode == 2) && terms->st_w != nullptr;
+    if constexpr (TERMS == 1) stw = (mode == 2) && terms->st_w != nullptr;
     R wpow = R(0);
     if constexpr (RB2 > 1) __syncthreads();
 #pragma unroll
@@ -484,8 +494,8 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
         }
         const int klo = rank * Ak + al;
         const int c = c0 + col;
-        float wv[TERMS ? RL : 1];                     // the loss weights of this thread's outputs, loaded first
-        if constexpr (TERMS) if (stw) {
+        float wv[TERMS == 1 ? RL : 1];                // the loss weights of this thread's outputs, loaded first
+        if constexpr (TERMS == 1) if (stw) {
 #pragma unroll
             for (int k = 0; k < RL; ++k) {
                 const int khi = (RB2 > 1) ? (hi + RB1 * k) : k;
@@ -498,22 +508,22 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             const int kk = klo + A * khi;             // natural frequency in [L]
             C y = v[u * RL + k];
             long long idx;
-            if constexpr (SPLIT) {
+            if constexpr (SPLIT != 0) {
                 const int cc = c0 + col;                      // the pass's view column
-                const int mC = (1 << sp->lgCc) - 1;
+                const int mC = (1 << sp->lgC) - 1;
                 if (sp->sub == 1) {                           // S[j_b][c][k_a], view column j_b C + c
                     y = cmul(y, E1[kk]);
                     idx = ((long long)cc << sp->lgLa) + kk;
                 } else if (sp->sub == 2) {                    // W[pi_m2(c)][k_a + La k_b], view column c La + k_a
                     y = cmul(y, cmul(E1[col], E2[kk]));
-                    const unsigned cw = (unsigned)(sp->c_start + (cc >> sp->lgLa));
+                    const unsigned cw = (unsigned)(cc >> sp->lgLa);
                     idx = (long long)digit_reverse(cw, sp->rev_bits_c, args.rev_t) * args.out_ld +
                           (cc & ((1 << sp->lgLa) - 1)) + ((long long)kk << sp->lgLa);
                 } else if (sp->sub == 3) {                    // S[j_b][k_a][v], view column j_b C + v
                     y = cmul(y, E1[kk]);
-                    idx = ((((long long)(c0 >> sp->lgCc) << sp->lgLa) + kk) << sp->lgCc) + (cc & mC);
+                    idx = ((((long long)(c0 >> sp->lgC) << sp->lgLa) + kk) << sp->lgC) + (cc & mC);
                 } else {                                      // y[k_a + La k_b][v], view column k_a C + v
-                    idx = (long long)((cc >> sp->lgCc) + (kk << sp->lgLa)) * args.out_ld + sp->c_start + (cc & mC);
+                    idx = (long long)((cc >> sp->lgC) + (kk << sp->lgLa)) * args.out_ld + (cc & mC);
                 }
             } else if (mode == 1) {
                 y = cmul(y, cmul(E1[(col << (ilog2c<A>::value - lgK)) + al], E2[(khi << lgW) + col]));
@@ -527,7 +537,13 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
                 }
             } else if (mode == 2) {
                 idx = (long long)kk * args.out_ld + c;
-                if constexpr (TERMS) if (stw) wpow += R(wv[k]) * (y.x * y.x + y.y * y.y);
+                if constexpr (TERMS == 1) if (stw) {
+                    wpow += R(wv[k]) * (y.x * y.x + y.y * y.y);
+                    if (terms->st_weighted) {
+                        y.x *= R(wv[k]);
+                        y.y *= R(wv[k]);
+                    }
+                }
             } else {
                 const unsigned arow = digit_reverse((unsigned)kk, args.rev_bits, args.rev_t);
                 idx = (long long)arow * args.out_ld + c;
@@ -536,7 +552,7 @@ __device__ __forceinline__ void stage_tile(const StageArgs &args, int tile, long
             st_cx(gout + idx, y);
         }
     }
-    if constexpr (TERMS) if (stw) {
+    if constexpr (TERMS == 1) if (stw) {
         if (NT & 31) {
             atomicAdd(terms->st_loss, (double)wpow);         // tiny tiles: one atomic per thread
         } else {
@@ -576,7 +592,7 @@ __global__ void __launch_bounds__(512, MINB) paco_stage_kernel_shard(const Stage
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int rank = 0;
     if ((1 << args.lgK) > 1) rank = (int)cg::this_cluster().block_rank();
-    stage_tile<R, A, B, -1, -1, 0, false, TC_NONE, false, true>(
+    stage_tile<R, A, B, -1, -1, 0, false, TC_NONE, 0, true>(
         args, (int)(blockIdx.x >> args.lgK), (long long)blockIdx.y * in_stride, rank, smem_raw, nullptr, &sh,
         (long long)blockIdx.y * out_stride);
 }
@@ -586,20 +602,20 @@ template <typename R, int A, int B, int MINB>
 __global__ void __launch_bounds__(512, MINB) paco_stage_kernel_split(const StageArgs args, const SplitArgs sp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stage_tile<R, A, B, -1, 0, 0, false, TC_NONE, false, false, true>(
-        args, (int)blockIdx.x, (long long)blockIdx.y * sp.in_stride, 0, smem_raw, nullptr, nullptr,
-        (long long)blockIdx.y * sp.out_stride, &sp);
+    stage_tile<R, A, B, -1, 0, 0, false, TC_NONE, 0, false, 1>(
+        args, (int)blockIdx.x, (long long)blockIdx.y * args.batch_stride, 0, smem_raw, nullptr, nullptr, 0, &sp);
 }
 
 // The generic stage with the element-wise terms of a weighted power loss
-// (StageTerms) compiled in; paco_stage_kernel carries none of their code.
-template <typename R, int A, int B, int MINB>
+// (StageTerms) compiled in -- TM = 1 all of them, TM = 2 the scalar factor on
+// Phase I's loads alone; paco_stage_kernel carries none of their code.
+template <typename R, int A, int B, int MINB, int TM = 1>
 __global__ void __launch_bounds__(512, MINB) paco_stage_kernel_terms(const StageArgs args, const StageTerms terms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int rank = 0;
     if ((1 << args.lgK) > 1) rank = (int)cg::this_cluster().block_rank();
-    stage_tile<R, A, B, -1, -1, 0, false, TC_NONE, true>(args, (int)(blockIdx.x >> args.lgK),
+    stage_tile<R, A, B, -1, -1, 0, false, TC_NONE, TM>(args, (int)(blockIdx.x >> args.lgK),
                                                          (long long)blockIdx.y * args.batch_stride, rank, smem_raw,
                                                          &terms);
 }

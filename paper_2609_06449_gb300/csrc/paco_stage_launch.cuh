@@ -7,7 +7,7 @@
 namespace paco {
 
 // lgL -> (A, B) = (2^ceil(lgL/2), 2^floor(lgL/2)), the balanced split.
-template <typename R, int LGL, bool TERMS>
+template <typename R, int LGL, int TERMS>
 struct StageKernel {
     static constexpr int A = 1 << ((LGL + 1) / 2);
     static constexpr int B = 1 << (LGL / 2);
@@ -16,9 +16,9 @@ struct StageKernel {
     static const void *fn(int minb)
     {
         if constexpr (B == 1) return TERMS ? nullptr : reinterpret_cast<const void *>(&paco_stage_kernel_b1<R, A>);
-        else if constexpr (TERMS) {
-            if (minb == 2) return reinterpret_cast<const void *>(&paco_stage_kernel_terms<R, A, B, 2>);
-            return reinterpret_cast<const void *>(&paco_stage_kernel_terms<R, A, B, 1>);
+        else if constexpr (TERMS != 0) {
+            if (minb == 2) return reinterpret_cast<const void *>(&paco_stage_kernel_terms<R, A, B, 2, TERMS>);
+            return reinterpret_cast<const void *>(&paco_stage_kernel_terms<R, A, B, 1, TERMS>);
         } else if constexpr (sizeof(R) == 4) {
             if (minb == 2) return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B, -1, -1, 0, 2>);
             return reinterpret_cast<const void *>(&paco_stage_kernel<R, A, B>);
@@ -63,9 +63,10 @@ const void *stage_kernel_fn_split(int lgL, int minb)
 #undef PACO_SPLIT_CASE
 }
 
-// The generic stage kernel for length 2^lgL; TERMS = true: the variant with
-// the weighted-loss terms (StageArgs::ld_w, st_w) compiled in.
-template <typename R, bool TERMS = false>
+// The generic stage kernel for length 2^lgL; TERMS = 1: the variant with the
+// weighted-loss terms (StageTerms) compiled in, 2: with the scalar factor on
+// Phase I's loads alone.
+template <typename R, int TERMS = 0>
 const void *stage_kernel_fn(int lgL, int minb)
 {
     switch (lgL) {

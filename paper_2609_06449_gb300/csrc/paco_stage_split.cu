@@ -1,4 +1,4 @@
-// Stage kernels for the passes of a split stage (complex64, lengths 2^5..2^7).
+// Stage kernels for the passes of a split stage (complex64, lengths 2^5..2^8).
 #include "paco_stage_launch.cuh"
 
 namespace paco {

@@ -146,3 +146,33 @@ def test_fused_loss_rejects_panel_plans():
     with pytest.raises(paco.PacoError) as e:
         paco.weighted_power_loss(x, w, N1, N2, 2)
     assert e.value.status == 2                               # PACO_ERR_UNSUPPORTED
+
+
+def test_weighted_entry_points_directly():
+    """The two C-ABI calls behind weighted_power_loss, each form:
+    out_weighted = 0 / 1 (y or w * y stored, the loss the same) and the
+    weighted input with a weight array, with a scalar only, and with both."""
+    N1 = N2 = 64
+    N, batch = N1 * N2, 3
+    plan = paco.Plan(N1, N2, 2, batch, paco.C64)
+    xh = gaussian(batch * N, 31, np.complex64).reshape(batch, N)
+    wh = weights(batch * N, 32).reshape(batch, N)
+    x = torch.from_numpy(xh).cuda()
+    w = torch.from_numpy(wh).cuda()
+    y = torch.empty_like(x)
+    u = torch.empty_like(x)
+    l0 = torch.empty((), dtype=torch.float64, device="cuda")
+    l1 = torch.empty((), dtype=torch.float64, device="cuda")
+    plan.execute_weighted_power(x, y, w, l0, -1)
+    plan.execute_weighted_power(x, u, w, l1, -1, out_weighted=True)
+    yo = oracle.fft(xh.astype(np.complex128))
+    want = float(np.sum(wh * np.abs(yo) ** 2))
+    assert abs(l0.item() - want) <= 1e-6 * want and abs(l1.item() - want) <= 1e-6 * want
+    assert np.allclose(u.cpu().numpy(), wh * y.cpu().numpy(), rtol=1e-6, atol=1e-6 * np.abs(yo).max())
+    g = torch.full((), 0.75, dtype=torch.float64, device="cuda")
+    for wt, sc, mult, factor in ((w, None, 3.0, 3.0 * wh), (None, g, 2.0, 1.5), (w, g, 2.0, 1.5 * wh)):
+        out = torch.empty_like(x)
+        plan.execute_weighted_input(x, out, wt, sc, mult, +1)
+        ref = oracle.fft(factor * xh.astype(np.complex128), +1)
+        err = np.linalg.norm(out.cpu().numpy() - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert float(err.max()) <= 5e-7 * math.log2(N)

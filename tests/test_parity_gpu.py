@@ -176,11 +176,10 @@ def test_split_stages_against_oracle(N1, N2, b, batch, split, d):
 @pytest.mark.parametrize("N1,N2,b,batch", [(16384, 2048, 2, 2), (16384, 4096, 4, 1), (4096, 16384, 4, 2),
                                             (16384, 512, 2, 1), (16384, 16384, 4, 1)])
 @pytest.mark.parametrize("d", [-1, 1])
-def test_split_2p14_in_column_chunks(N1, N2, b, batch, d):
-    """split=1: 2^14 stages as two passes per chunk of 256 columns (the
-    intermediate in two chunk buffers that alternate) -- every transform
-    element by element against the oracle, both directions, three times (a
-    race between the chunks would show as a run that differs)."""
+def test_split_2p14_option(N1, N2, b, batch, d):
+    """split=1: the 2^14 stages as two passes too (2^8 x 2^6 for b = 4, 2^7 x
+    2^7 for b = 2) -- every transform element by element against the oracle,
+    both directions, three times with identical results."""
     N = N1 * N2
     plan = paco.Plan(N1, N2, b, batch, paco.C64, split=1)
     want = tuple(int(L >= 4096) for L in (N1, N2))
