@@ -207,6 +207,7 @@ typedef struct {
     int rank;            /* this rank, in [0, G) */
     int64_t batch;
     paco_dtype_t dtype;  /* PACO_C64 */
+    int restore;         /* 1: also build the maps of paco_shard_restore_* */
 } paco_shard_opts_t;
 
 paco_status_t paco_plan_create_sharded(paco_plan_t **out, const paco_shard_opts_t *opts);
@@ -230,6 +231,36 @@ paco_status_t paco_shard_stage2(paco_plan_t *plan, const void *recv, void *y_loc
  */
 paco_status_t paco_probe_tc05_dft128(const void *x, void *y, int64_t batch, int64_t C, float *ms,
                                      paco_stream_t stream);
+
+/*
+ * Restoring the input's ownership -- the second redistribution the paper
+ * leaves out (Sect. 6, Limitations): after paco_shard_stage2 rank q holds
+ * y_local = Y[:, q K1 .. (q+1) K1) (K1 = N1/G); afterwards rank r holds y in
+ * the layout its input had, y viewed N1 x N2, columns j in [r Cl, (r+1) Cl)
+ * (Cl = N2/G): [batch][N1][Cl].  Element k of y moves from rank
+ * floor((k mod N1) / K1) to rank floor((k mod N2) / Cl); each block carries
+ * its items in increasing k.  Block sizes differ between pairs unless
+ * N1 = N2 (then every item stays on its rank).  Per rank:
+ *   paco_shard_restore_pack    y_local -> send, [G][batch][send_counts[r]]
+ *   (exchange)                 block r of every rank's send buffer to rank r,
+ *                              into block q (the sender) of its receive buffer,
+ *                              [G][batch][recv_counts[q]] (an all-to-all with
+ *                              uneven splits: counts times batch);
+ *   paco_shard_restore_unpack  recv -> x_layout, [batch][N1][Cl].
+ * The plan must be created with paco_shard_opts_t.restore = 1 (it then owns
+ * two int32 maps of N/G entries; N/G < 2^31); otherwise
+ * PACO_ERR_UNSUPPORTED.  Buffers: device, complex64, 8-byte aligned, in != out.
+ * paco_shard_restore_counts gives the block sizes per transform (G entries
+ * each, either pointer may be NULL).  paco_shard_restore_maps is the host
+ * computation of one rank's maps and counts (no device needed; arrays of
+ * N/G and G entries, NULL to skip), for tests and for callers that move the
+ * data themselves.
+ */
+paco_status_t paco_shard_restore_counts(const paco_plan_t *plan, int64_t *send_counts, int64_t *recv_counts);
+paco_status_t paco_shard_restore_pack(paco_plan_t *plan, const void *y_local, void *send, paco_stream_t stream);
+paco_status_t paco_shard_restore_unpack(paco_plan_t *plan, const void *recv, void *x_layout, paco_stream_t stream);
+paco_status_t paco_shard_restore_maps(int64_t N1, int64_t N2, int G, int rank, int32_t *pack_map,
+                                      int64_t *send_counts, int32_t *unpack_map, int64_t *recv_counts);
 
 /*
  * paco_execute_weighted_power -- paco_execute plus the weighted power of the

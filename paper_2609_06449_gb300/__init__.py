@@ -94,6 +94,7 @@ class ShardOpts(ctypes.Structure):
     _fields_ = [
         ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("b", ctypes.c_int), ("G", ctypes.c_int),
         ("rank", ctypes.c_int), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
+        ("restore", ctypes.c_int),
     ]
 
 
@@ -158,6 +159,15 @@ def _load():
         f = getattr(L, name)
         f.argtypes = [vp, vp, vp, i32, vp]
         f.restype = i32
+    p64, p32 = ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int32)
+    L.paco_shard_restore_counts.argtypes = [vp, p64, p64]
+    L.paco_shard_restore_counts.restype = i32
+    for name in ("paco_shard_restore_pack", "paco_shard_restore_unpack"):
+        f = getattr(L, name)
+        f.argtypes = [vp, vp, vp, vp]
+        f.restype = i32
+    L.paco_shard_restore_maps.argtypes = [i64, i64, i32, i32, p32, p64, p32, p64]
+    L.paco_shard_restore_maps.restype = i32
     L.paco_probe_tc05_dft128.argtypes = [vp, vp, i64, i64, ctypes.POINTER(ctypes.c_float), vp]
     L.paco_probe_tc05_dft128.restype = i32
     L.paco_noalloc_check.argtypes = []

@@ -409,6 +409,7 @@ extern "C" void paco_plan_destroy(paco_plan_t *pl)
 {
     if (!pl) return;
     batched_destroy(pl->bs);
+    restore_destroy(pl);
     cudaFree(pl->tc);
     cudaFree(pl->twL1);
     cudaFree(pl->twL2);
@@ -676,7 +677,18 @@ extern "C" paco_status_t paco_plan_create_sharded(paco_plan_t **out, const paco_
     paco_plan_opts_t po;
     memset(&po, 0, sizeof(po));
     po.N1 = o->N1; po.N2 = o->N2; po.b = o->b; po.p = o->G; po.batch = o->batch; po.dtype = o->dtype;
-    return plan_build(out, &po, o->G, o->rank);
+    paco_status_t st = plan_build(out, &po, o->G, o->rank);
+    if (st != PACO_OK || !o->restore) return st;
+    if ((o->N1 * o->N2) / o->G > INT32_MAX) {
+        paco_plan_destroy(*out);
+        *out = nullptr;
+        return fail(PACO_ERR_UNSUPPORTED, "restore: N/G must stay below 2^31");
+    }
+    if ((st = restore_setup(*out)) != PACO_OK) {
+        paco_plan_destroy(*out);
+        *out = nullptr;
+    }
+    return st;
 }
 
 static paco_status_t launch_shard(const paco_plan *pl, int mode, const void *in, void *out, int dir,

@@ -61,6 +61,9 @@ struct paco_plan {
     void *split_scratch = nullptr; // split stages: the intermediate of their two passes (N * batch)
     int shard_G = 0;               // sharded form (paco_plan_create_sharded): ranks, 0 = not sharded
     int shard_rank = 0;
+    void *rs_maps = nullptr;       // restoring the input's ownership (paco_restore.cu): pack and unpack maps
+    void *rs_off = nullptr;        //   their block offsets (send, then receive; G + 1 each)
+    int64_t *rs_send_counts = nullptr, *rs_recv_counts = nullptr;   // host copies of the block sizes
     // uneven batch (paco_plan_create_batched): N = total elements, batch = 1
     paco::BatchedState *bs = nullptr;
 };
@@ -86,6 +89,10 @@ bool cluster_eligible(const paco_plan *pl);
 paco_status_t cluster_setup(paco_plan *pl);
 paco_status_t launch_cluster(const paco_plan *pl, const void *in, void *out, int dir, unsigned *pair_count,
                              cudaStream_t stream);
+
+// paco_restore.cu
+paco_status_t restore_setup(paco_plan *pl);
+void restore_destroy(paco_plan *pl);
 
 // paco_batched.cu
 paco_status_t batched_execute(paco_plan *pl, const void *in, void *out, int dir, cudaStream_t stream);

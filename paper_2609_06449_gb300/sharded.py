@@ -11,9 +11,12 @@ Y = y viewed N2 x N1, K1 = N1/G); the layouts are those of
 blocks of N/G^2 items per transform (``paco_shard_stage1``), one all-to-all
 of equal blocks (``torch.distributed.all_to_all_single``, NCCL grouped
 send/recv for CUDA tensors: every rank receives into its own buffer, no peer
-loads), Phase III on the received blocks (``paco_shard_stage2``).  The stage
-and exchange callables can be replaced, which is how the orchestration is
-tested without GPUs."""
+loads), Phase III on the received blocks (``paco_shard_stage2``).
+``sharded_restore`` is the optional second redistribution that gives every
+rank the input's slab of y ([batch][N1][Cl]): pack, an all-to-all with
+uneven splits, unpack (``paco_shard_restore_*``).  The stage, pack and
+exchange callables can be replaced, which is how the orchestration is tested
+without GPUs."""
 
 from __future__ import annotations
 
@@ -22,11 +25,27 @@ import ctypes
 from . import C64, ShardOpts, _check, _ptr, _stream, lib
 
 
-class ShardedPlan:
-    """``paco_plan_create_sharded``: the plan of rank ``rank`` of ``G``."""
+def restore_maps(N1: int, N2: int, G: int, rank: int):
+    """``paco_shard_restore_maps`` (host): (pack_map, send_counts, unpack_map,
+    recv_counts) of one rank as numpy arrays."""
+    import numpy as np
+    n = int(N1) * int(N2) // int(G)
+    pack = np.empty(n, np.int32)
+    unpack = np.empty(n, np.int32)
+    sc = np.empty(int(G), np.int64)
+    rc = np.empty(int(G), np.int64)
+    p32, p64 = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)
+    _check(lib.paco_shard_restore_maps(int(N1), int(N2), int(G), int(rank), pack.ctypes.data_as(p32),
+                                       sc.ctypes.data_as(p64), unpack.ctypes.data_as(p32), rc.ctypes.data_as(p64)))
+    return pack, sc, unpack, rc
 
-    def __init__(self, N1: int, N2: int, b: int, G: int, rank: int, batch: int = 1):
-        o = ShardOpts(int(N1), int(N2), int(b), int(G), int(rank), int(batch), C64)
+
+class ShardedPlan:
+    """``paco_plan_create_sharded``: the plan of rank ``rank`` of ``G``
+    (``restore``: also the maps of the second redistribution)."""
+
+    def __init__(self, N1: int, N2: int, b: int, G: int, rank: int, batch: int = 1, restore: bool = False):
+        o = ShardOpts(int(N1), int(N2), int(b), int(G), int(rank), int(batch), C64, 1 if restore else 0)
         h = ctypes.c_void_p()
         _check(lib.paco_plan_create_sharded(ctypes.byref(h), ctypes.byref(o)))
         self._h = h
@@ -39,6 +58,19 @@ class ShardedPlan:
 
     def stage2(self, recv, y_local, dir: int = -1, stream=None) -> None:
         _check(lib.paco_shard_stage2(self._h, _ptr(recv), _ptr(y_local), int(dir), _stream(stream)))
+
+    def restore_counts(self):
+        """(send_counts, recv_counts) per transform, G entries each."""
+        sc = (ctypes.c_int64 * self.G)()
+        rc = (ctypes.c_int64 * self.G)()
+        _check(lib.paco_shard_restore_counts(self._h, sc, rc))
+        return list(sc), list(rc)
+
+    def restore_pack(self, y_local, send, stream=None) -> None:
+        _check(lib.paco_shard_restore_pack(self._h, _ptr(y_local), _ptr(send), _stream(stream)))
+
+    def restore_unpack(self, recv, out, stream=None) -> None:
+        _check(lib.paco_shard_restore_unpack(self._h, _ptr(recv), _ptr(out), _stream(stream)))
 
     def close(self) -> None:
         if getattr(self, "_h", None):
@@ -90,3 +122,43 @@ def sharded_fft(x_local, N1: int, N2: int, b: int, dir: int = -1, group=None, st
     y_local = torch.empty(batch * N2 * K1, dtype=x_local.dtype, device=x_local.device)
     stage2(recv, y_local, dir)
     return y_local.reshape(batch, N2, K1)
+
+
+def exchange_uneven(send, recv, send_splits, recv_splits, group=None) -> None:
+    """All-to-all with uneven blocks: send_splits[r] items of ``send`` to rank
+    r, recv_splits[q] items from rank q into ``recv`` (complex buffers travel
+    as their real view)."""
+    import torch
+    import torch.distributed as dist
+    f = 2 if send.is_complex() else 1
+    s = torch.view_as_real(send).reshape(-1) if send.is_complex() else send
+    r = torch.view_as_real(recv).reshape(-1) if recv.is_complex() else recv
+    dist.all_to_all_single(r, s, output_split_sizes=[f * int(c) for c in recv_splits],
+                           input_split_sizes=[f * int(c) for c in send_splits], group=group)
+
+
+def sharded_restore(y_local, N1: int, N2: int, group=None, plan=None, pack=None, unpack=None, counts=None,
+                    exchange=exchange_uneven):
+    """The second redistribution: from this rank's output slab y_local
+    ([batch][N2][K1], the result of ``sharded_fft``) to the input's
+    ownership of y ([batch][N1][Cl]: y viewed N1 x N2, columns [rank Cl,
+    (rank+1) Cl)).  pack(y_local, send), unpack(recv, out) and counts() ->
+    (send_counts, recv_counts) per transform default to ``plan`` (a
+    ShardedPlan created with restore=True)."""
+    import torch
+    import torch.distributed as dist
+    G = dist.get_world_size(group)
+    N1, N2 = int(N1), int(N2)
+    n = N1 * N2 // G
+    batch = y_local.numel() // n
+    if plan is not None:
+        pack, unpack, counts = pack or plan.restore_pack, unpack or plan.restore_unpack, counts or plan.restore_counts
+    sc, rc = counts()
+    y_local = y_local.contiguous()
+    send = torch.empty(batch * n, dtype=y_local.dtype, device=y_local.device)
+    pack(y_local, send)
+    recv = torch.empty_like(send)
+    exchange(send, recv, [batch * c for c in sc], [batch * c for c in rc], group)
+    out = torch.empty(batch * n, dtype=y_local.dtype, device=y_local.device)
+    unpack(recv, out)
+    return out.reshape(batch, N1, N2 // G)

@@ -110,3 +110,109 @@ def test_sharded_fft_orchestration_over_gloo(G, N1, N2, b, dir):
     x = gaussian(batch * N, 50 + G, np.complex128).reshape(batch, -1)
     ref = oracle.fft(x, dir)
     assert np.max(np.abs(y - ref)) <= 1e-9 * np.sqrt(N) * np.max(np.abs(ref))
+
+
+# ---- restoring the input's ownership (the second redistribution) ----------
+
+def _restore_by_maps(y, N1, N2, G, batch):
+    """Every rank's pack, the uneven exchange by hand, every rank's unpack,
+    with the host maps of paco_shard_restore_maps (numpy data movement)."""
+    from paper_2609_06449_gb300.sharded import restore_maps
+    K1, Cl = N1 // G, N2 // G
+    Y = y.reshape(batch, N2, N1)
+    maps = [restore_maps(N1, N2, G, q) for q in range(G)]
+    sends = []
+    for q in range(G):
+        yl = np.ascontiguousarray(Y[:, :, q * K1:(q + 1) * K1]).reshape(batch, -1)
+        pack, sc, _, _ = maps[q]
+        off = np.concatenate([[0], np.cumsum(sc)])
+        sends.append([yl[:, pack[off[r]:off[r + 1]]] for r in range(G)])   # block r: [batch][count]
+    outs = []
+    for r in range(G):
+        _, _, unpack, rc = maps[r]
+        off = np.concatenate([[0], np.cumsum(rc)])
+        out = np.zeros((batch, N1 * Cl), complex)
+        for q in range(G):
+            blk = sends[q][r]
+            assert blk.shape[1] == rc[q]                     # the sizes agree on both sides
+            out[:, unpack[off[q]:off[q + 1]]] = blk
+        outs.append(out.reshape(batch, N1, Cl))
+    return outs
+
+
+@pytest.mark.parametrize("N1,N2,G", [(16, 16, 4), (64, 16, 4), (16, 64, 4), (32, 8, 2), (8, 32, 8),
+                                     (256, 64, 16), (128, 512, 4)])
+def test_restore_maps_move_every_item_to_the_input_owner(N1, N2, G):
+    """The maps of the second redistribution, by full simulation: rank r ends
+    with y viewed N1 x N2, columns [r Cl, (r+1) Cl); every item moves once;
+    with N1 = N2 nothing leaves its rank."""
+    batch = 2
+    rng = np.random.default_rng(N1 + N2 + G)
+    y = rng.standard_normal((batch, N1 * N2)) + 1j * rng.standard_normal((batch, N1 * N2))
+    outs = _restore_by_maps(y, N1, N2, G, batch)
+    Cl = N2 // G
+    for r in range(G):
+        assert np.array_equal(outs[r], y.reshape(batch, N1, N2)[:, :, r * Cl:(r + 1) * Cl])
+    if N1 == N2:
+        from paper_2609_06449_gb300.sharded import restore_maps
+        for q in range(G):
+            sc = restore_maps(N1, N2, G, q)[1]
+            assert sc[q] == N1 * N2 // G and sc.sum() == sc[q]
+
+
+def _restore_worker(rank, G, port, N1, N2, q):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(G))
+    import paper_2609_06449_gb300.sharded as sharded
+    dist.init_process_group("gloo")
+    try:
+        batch, K1 = 2, N1 // G
+        rng = np.random.default_rng(5)
+        y = rng.standard_normal((batch, N1 * N2)) + 1j * rng.standard_normal((batch, N1 * N2))
+        yl = torch.from_numpy(np.ascontiguousarray(y.reshape(batch, N2, N1)[:, :, rank * K1:(rank + 1) * K1]))
+        pack, sc, unpack, rc = sharded.restore_maps(N1, N2, G, rank)
+        offs = np.concatenate([[0], np.cumsum(sc)])
+        offr = np.concatenate([[0], np.cumsum(rc)])
+
+        def do_pack(src, send):                      # [G][batch][count]
+            v = src.reshape(batch, -1).numpy()
+            send.copy_(torch.from_numpy(np.concatenate(
+                [v[:, pack[offs[r]:offs[r + 1]]].reshape(-1) for r in range(G)])))
+
+        def do_unpack(recv, out):
+            rv = recv.numpy()
+            o = np.zeros((batch, N1 * N2 // G), complex)
+            start = 0
+            for qq in range(G):
+                n = batch * rc[qq]
+                o[:, unpack[offr[qq]:offr[qq + 1]]] = rv[start:start + n].reshape(batch, rc[qq])
+                start += n
+            out.copy_(torch.from_numpy(o.reshape(-1)))
+
+        got = sharded.sharded_restore(yl, N1, N2, pack=do_pack, unpack=do_unpack,
+                                      counts=lambda: (list(sc), list(rc)))
+        q.put((rank, got.numpy().copy()))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("G,N1,N2", [(2, 32, 8), (4, 16, 64)])
+def test_sharded_restore_orchestration_over_gloo(G, N1, N2):
+    """sharded_restore over gloo: the uneven all-to-all delivers every block,
+    and each rank ends with the input's slab of y."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_restore_worker, args=(r, G, port, N1, N2, q)) for r in range(G)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(G))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    batch, Cl = 2, N2 // G
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((batch, N1 * N2)) + 1j * rng.standard_normal((batch, N1 * N2))
+    for r in range(G):
+        assert np.array_equal(got[r], y.reshape(batch, N1, N2)[:, :, r * Cl:(r + 1) * Cl])
