@@ -367,3 +367,12 @@ def test_permute_rejects_aliasing():
     xt = torch.zeros(4096, dtype=torch.complex64, device="cuda")
     with pytest.raises(paco.PacoError):
         plan.permute(xt, xt)
+
+
+def test_fp64_peak_probe_is_plausible():
+    """paco_probe_fp64_peak (the complex128 roofline's denominator): a DFMA
+    rate between a tenth and twice GB300's nominal 1.25 TFLOP/s, over a
+    launch long enough to time."""
+    gflops, ms = paco.probe_fp64_peak(iters=1024)
+    assert ms > 0.05
+    assert 125.0 <= gflops <= 2500.0, gflops
