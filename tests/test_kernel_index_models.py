@@ -582,3 +582,125 @@ def test_cluster_kernel_model(K, p, b, conj):
                 y[k2 * L + r * W2 + vl] = np.conj(outs[tid][k]) if conj else outs[tid][k]
     want = np.fft.fft(x) if not conj else np.fft.ifft(x) * N
     assert np.allclose(y, want, atol=1e-8 * np.sqrt(N))
+
+
+# ---- the tcgen05 probe: operand layout vs the MMA descriptor's addressing ---
+
+def _sw128_off(r, k, R):
+    """The kernel's byte offset of element (row r, k) of a K-major bf16
+    operand with K = 128 in the 128-byte swizzle layout."""
+    return (k >> 6) * (R * 128) + r * 128 + ((((k & 63) >> 3) ^ (r & 7)) << 4) + ((k & 7) << 1)
+
+
+def _descriptor_address(start, r, kp):
+    """Address the MMA reads for element (r, kp) of one K = 16 step from a
+    descriptor with this start, stride byte offset 1024 and the 128-byte
+    swizzle: 8-row groups 1024 B apart, rows 128 B apart, then address bits
+    [4:6] XOR bits [7:9]."""
+    a = start + (r >> 3) * 1024 + (r & 7) * 128 + (kp >> 3) * 16 + (kp & 7) * 2
+    return a ^ (((a >> 7) & 7) << 4)
+
+
+@pytest.mark.parametrize("R", [128, 64, 32])
+def test_tc05_operand_layout_matches_descriptors(R):
+    """The layout the tcgen05 kernel writes (and the table kernel builds) is
+    what its descriptors address: for every K = 16 step kk (start = atom
+    (kk / 4) + 32 B (kk mod 4)) and every element, and it is a bijection onto
+    the operand's R * 256 bytes."""
+    seen = set()
+    for r in range(R):
+        for k in range(128):
+            o = _sw128_off(r, k, R)
+            assert 0 <= o < R * 256
+            seen.add(o)
+    assert len(seen) == R * 128
+    for kk in range(8):
+        start = (kk >> 2) * (R * 128) + (kk & 3) * 32
+        for r in range(R):
+            for kp in range(16):
+                assert _descriptor_address(start, r, kp) == _sw128_off(r, 16 * kk + kp, R)
+
+
+# ---- the split stages: the four passes' address maps compose to the DFT ------
+
+@pytest.mark.parametrize("N1,N2,b", [(64, 32, 2), (64, 64, 4), (128, 64, 2), (256, 16, 4)])
+@pytest.mark.parametrize("conj", [False, True])
+def test_split_stage_address_maps(N1, N2, b, conj):
+    """Both stages as their two passes with the kernels' formulas: Phase I
+    pass A (x viewed [La][Lb C], twiddle w_L^{-k_a j_b}, S[j_b][c][k_a]),
+    pass B (S rows j_b, w_N^{-k1 c}, W[pi_m2(c)][k_a + La k_b]), Phase III
+    pass A (W row pi(j_a) of block pi(j_b), S[j_b][k_a][v]) and pass B
+    (y[k_a + La k_b][v]); every slot written once; the result the DFT."""
+    import oracle
+    t = {2: 1, 4: 2, 8: 3, 16: 4}[b]
+    N = N1 * N2
+    rng = np.random.default_rng(N1 + N2 + b)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    xin = np.conj(x) if conj else x
+
+    def split(L):
+        lgL = L.bit_length() - 1
+        lgLa = (lgL + 1) // 2
+        while lgLa % t:
+            lgLa += 1
+        return 1 << lgLa, L >> lgLa
+
+    def rev(u, bits):
+        return int(oracle.digit_reverse_table(b, bits // t)[u]) if bits else 0
+
+    def twL(L, r):
+        return np.exp(-2j * np.pi * (r % L) / L)
+
+    # Phase I (L = N1 over C = N2 columns)
+    L, C = N1, N2
+    La, Lb = split(L)
+    lgC = C.bit_length() - 1
+    S = np.full(N, np.nan, complex)
+    X = xin.reshape(L, C)
+    for cc in range(Lb * C):                             # view column j_b C + c
+        jb, c = cc >> lgC, cc & (C - 1)
+        col = np.array([X[ja * Lb + jb, c] for ja in range(La)])   # row j_a of [La][Lb C]
+        A = np.fft.fft(col)
+        for ka in range(La):
+            idx = cc * La + ka
+            assert np.isnan(S[idx])
+            S[idx] = A[ka] * twL(L, ka * jb)
+    W = np.full(N, np.nan, complex)
+    lgN2 = lgC
+    for cc in range(C * La):                             # view column c La + k_a
+        c, ka = cc // La, cc % La
+        col = np.array([S[jb * (C * La) + cc] for jb in range(Lb)])
+        B = np.fft.fft(col)
+        for kb in range(Lb):
+            k1 = ka + La * kb
+            idx = rev(c, lgN2) * L + k1
+            assert np.isnan(W[idx])
+            W[idx] = B[kb] * np.exp(-2j * np.pi * ((k1 * c) % N) / N)
+    # Phase III (L = N2 over C = N1 columns), W as [N2][N1]
+    L, C = N2, N1
+    La, Lb = split(L)
+    lgC = C.bit_length() - 1
+    lgLa, lgLb = La.bit_length() - 1, Lb.bit_length() - 1
+    S = np.full(N, np.nan, complex)
+    for cc in range(Lb * C):                             # view column j_b C + v
+        jb, v = cc >> lgC, cc & (C - 1)
+        base = rev(jb, lgLb) * La * C + v
+        col = np.array([W[rev(ja, lgLa) * C + base] for ja in range(La)])
+        A = np.fft.fft(col)
+        for ka in range(La):
+            idx = ((jb * La + ka) * C) + v
+            assert np.isnan(S[idx])
+            S[idx] = A[ka] * twL(L, ka * jb)
+    y = np.full(N, np.nan, complex)
+    for cc in range(La * C):                             # view column k_a C + v
+        ka, v = cc >> lgC, cc & (C - 1)
+        col = np.array([S[jb * (La * C) + cc] for jb in range(Lb)])
+        B = np.fft.fft(col)
+        for kb in range(Lb):
+            idx = (ka + La * kb) * N1 + v
+            assert np.isnan(y[idx])
+            y[idx] = B[kb]
+    if conj:
+        y = np.conj(y)
+    want = np.fft.fft(x) if not conj else np.fft.ifft(x) * N
+    assert np.allclose(y, want, atol=1e-9 * np.sqrt(N) * np.abs(want).max())
