@@ -94,6 +94,12 @@ typedef struct {
                             N * batch scratch (paco_plan_info.stage_split): 0 =
                             default (2^12, 2^13; 2^14 keeps the L2 panel pipeline),
                             1 = 2^14 as well, -1 = never */
+    int dims;            /* 0 or 1: the 1-D DFT of length N (the paper's transform);
+                            2: the 2-D DFT of the N1 x N2 view, out[k2][k1] =
+                            sum_{j1,j2} x[j1 N2 + j2] w_N1^{-k1 j1} w_N2^{-k2 j2},
+                            i.e. returned transposed (N2 x N1 row-major) -- the
+                            same pipeline without the top-level twiddle: a slab
+                            decomposition of the 2-D FFT with one redistribution */
 } paco_plan_opts_t;
 
 /* Read-only description of a plan (paco_plan_info). */
@@ -115,6 +121,7 @@ typedef struct {
     int shard_rank;              /* sharded plan: this rank */
     int stage_split[2];          /* 1: the stage runs as two passes through the plan's
                                     N * batch scratch (complex64 stages of 2^12, 2^13) */
+    int dims;                    /* 1: the 1-D DFT; 2: the 2-D DFT of the N1 x N2 view */
 } paco_plan_info_t;
 
 /*
@@ -208,6 +215,8 @@ typedef struct {
     int64_t batch;
     paco_dtype_t dtype;  /* PACO_C64 */
     int restore;         /* 1: also build the maps of paco_shard_restore_* */
+    int dims;            /* 2: the 2-D DFT of the N1 x N2 view (as paco_plan_opts_t.dims):
+                            the slab-decomposed 2-D FFT across the G ranks */
 } paco_shard_opts_t;
 
 paco_status_t paco_plan_create_sharded(paco_plan_t **out, const paco_shard_opts_t *opts);

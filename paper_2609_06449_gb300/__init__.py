@@ -9,7 +9,8 @@ Entry points (same names as the C ABI):
 
 * ``Plan(N1, N2, b, batch, dtype, p=0, tile_w=0, cluster=0)`` --
   ``paco_plan_create_ex``; ``.execute(in_ptr, out_ptr, dir, stream)`` etc.
-* ``fft(x, N1, N2, b, p=0, dir=-1)`` -- torch tensors on the GPU.
+* ``fft(x, N1, N2, b, p=0, dir=-1)`` -- torch tensors on the GPU;
+  ``fft2`` -- the 2-D DFT of the N1 x N2 view (transposed result).
 * ``PacoFFT`` -- ``torch.autograd.Function`` whose backward is the conjugate
   transform (``dir=+1``).
 * ``sharded`` -- the sharded form across G ranks (``ShardedPlan``,
@@ -32,6 +33,7 @@ __all__ = [
     "lib",
     "library_path",
     "fft",
+    "fft2",
     "PacoFFT",
     "PacoWeightedPowerLoss",
     "weighted_power_loss",
@@ -70,7 +72,7 @@ class PlanOpts(ctypes.Structure):
         ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("b", ctypes.c_int),
         ("p", ctypes.c_int), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
         ("tile_w", ctypes.c_int), ("cluster", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-        ("split", ctypes.c_int),
+        ("split", ctypes.c_int), ("dims", ctypes.c_int),
     ]
 
 
@@ -87,6 +89,7 @@ class PlanInfo(ctypes.Structure):
         ("shard_G", ctypes.c_int),
         ("shard_rank", ctypes.c_int),
         ("stage_split", ctypes.c_int * 2),
+        ("dims", ctypes.c_int),
     ]
 
 
@@ -94,7 +97,7 @@ class ShardOpts(ctypes.Structure):
     _fields_ = [
         ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("b", ctypes.c_int), ("G", ctypes.c_int),
         ("rank", ctypes.c_int), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
-        ("restore", ctypes.c_int),
+        ("restore", ctypes.c_int), ("dims", ctypes.c_int),
     ]
 
 
@@ -236,9 +239,10 @@ class Plan:
     for torch's current stream."""
 
     def __init__(self, N1: int, N2: int, b: int, batch: int = 1, dtype: int = C64,
-                 p: int = 0, tile_w: int = 0, cluster: int = 0, ctas_per_sm: int = 0, split: int = 0):
+                 p: int = 0, tile_w: int = 0, cluster: int = 0, ctas_per_sm: int = 0, split: int = 0,
+                 dims: int = 1):
         o = PlanOpts(int(N1), int(N2), int(b), int(p), int(batch), int(dtype),
-                     int(tile_w), int(cluster), int(ctas_per_sm), int(split))
+                     int(tile_w), int(cluster), int(ctas_per_sm), int(split), int(dims))
         h = ctypes.c_void_p()
         _check(lib.paco_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))
         self._h = h
@@ -362,7 +366,7 @@ def _dtype_code(t) -> int:
 
 
 def get_plan(N1: int, N2: int, b: int, batch: int, dtype: int, p: int = 0,
-             device: int | None = None, stream: int | None = None) -> Plan:
+             device: int | None = None, stream: int | None = None, dims: int = 1) -> Plan:
     """The cached plan for this shape on ``device`` and ``stream``.
 
     A plan's executions must not overlap in time (the 2^14 complex64 panel
@@ -373,11 +377,11 @@ def get_plan(N1: int, N2: int, b: int, batch: int, dtype: int, p: int = 0,
     dev = torch.cuda.current_device() if device is None else device
     if stream is None:
         stream = int(torch.cuda.current_stream(dev).cuda_stream)
-    key = (N1, N2, b, batch, dtype, p, dev, int(stream))
+    key = (N1, N2, b, batch, dtype, p, dev, int(stream), int(dims))
     pl = _PLANS.get(key)
     if pl is None:
         with torch.cuda.device(dev):
-            pl = Plan(N1, N2, b, batch, dtype, p)
+            pl = Plan(N1, N2, b, batch, dtype, p, dims=dims)
         _PLANS[key] = pl
     return pl
 
@@ -390,6 +394,29 @@ def probe_tc05_dft128(x, y, batch: int, C: int, stream=None, timed: bool = False
     _check(lib.paco_probe_tc05_dft128(_ptr(x), _ptr(y), int(batch), int(C),
                                       ctypes.byref(ms) if timed else None, _stream(stream)))
     return ms.value if timed else None
+
+
+def fft2(x, N1: int, N2: int, b: int, p: int = 0, dir: int = -1, out=None):
+    """2-D DFT of every N1 x N2 array in ``x`` (last dimension N1*N2, row
+    major), returned transposed: out[..., k2 * N1 + k1] = sum_{j1, j2}
+    x[..., j1 * N2 + j2] w_N1^{dir k1 j1} w_N2^{dir k2 j2} (a plan with
+    dims = 2: the PACO pipeline without its top-level twiddle)."""
+    import torch
+    if not x.is_cuda:
+        raise ValueError("PACO runs on the GPU: x must be a CUDA tensor")
+    N = int(N1) * int(N2)
+    if x.shape[-1] != N:
+        raise ValueError(f"last dimension {x.shape[-1]} != N1*N2 = {N}")
+    x = x.contiguous()
+    batch = x.numel() // N
+    if out is None:
+        out = torch.empty_like(x)
+    dev = x.device.index
+    stream = int(torch.cuda.current_stream(x.device).cuda_stream)
+    with torch.cuda.device(dev):
+        pl = get_plan(int(N1), int(N2), int(b), batch, _dtype_code(x), int(p), dev, stream, dims=2)
+        pl.execute(x, out, dir, stream)
+    return out
 
 
 def fft(x, N1: int, N2: int, b: int, p: int = 0, dir: int = -1, out=None):

@@ -313,6 +313,11 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
     pl->shard_G = shard_G;
     pl->shard_rank = shard_rank;
     pl->req_split = o->split;
+    if (o->dims != 0 && o->dims != 1 && o->dims != 2) {
+        delete pl;
+        return fail(PACO_ERR_INVALID_ARG, "dims=%d must be 1 or 2", o->dims);
+    }
+    pl->dims = (o->dims == 2) ? 2 : 1;
     pl->req_ctas = o->ctas_per_sm;
     pl->form = (o->dtype == PACO_C64_TC_BF16X3) ? TC_BF16X3 : (o->dtype == PACO_C64_TC_FP16) ? TC_FP16 : TC_NONE;
     if (pl->form) {
@@ -334,14 +339,16 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
         return st;
     }
     // FP64-generated twiddle tables: w_N1^{-r}, w_N2^{-r}, and w_N^{-r} in
-    // two levels (r = hi * 2^h + lo).
+    // two levels (r = hi * 2^h + lo).  The 2-D DFT has no top-level twiddle:
+    // its w_N tables are w_1 = 1 (every kernel then multiplies by one).
     const int lgN = l1 + l2;
     pl->twN_lo_bits = (lgN + 1) / 2;
     const long long nlo = 1LL << pl->twN_lo_bits, nhi = (1LL << lgN) / nlo;
+    const long long Mtw = (pl->dims == 2) ? 1 : pl->N;
     if ((st = gen_table(pl->esize, &pl->twL1, pl->N1, pl->N1, 1, 0)) != PACO_OK ||
         (st = gen_table(pl->esize, &pl->twL2, pl->N2, pl->N2, 1, 0)) != PACO_OK ||
-        (st = gen_table(pl->esize, &pl->twN_lo, pl->N, nlo, 1, 0)) != PACO_OK ||
-        (st = gen_table(pl->esize, &pl->twN_hi, pl->N, nhi, nlo, 0)) != PACO_OK) {
+        (st = gen_table(pl->esize, &pl->twN_lo, Mtw, nlo, 1, 0)) != PACO_OK ||
+        (st = gen_table(pl->esize, &pl->twN_hi, Mtw, nhi, nlo, 0)) != PACO_OK) {
         paco_plan_destroy(pl);
         return st;
     }
@@ -447,6 +454,7 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
     info->shard_rank = pl->shard_rank;
     info->stage_split[0] = pl->st[0].split;
     info->stage_split[1] = pl->st[1].split;
+    info->dims = pl->dims;
     for (int s = 0; s < 2; ++s) {
         info->stage_tile_w[s] = 1 << pl->st[s].lgW;
         info->stage_cluster[s] = 1 << pl->st[s].lgK;
@@ -677,6 +685,7 @@ extern "C" paco_status_t paco_plan_create_sharded(paco_plan_t **out, const paco_
     paco_plan_opts_t po;
     memset(&po, 0, sizeof(po));
     po.N1 = o->N1; po.N2 = o->N2; po.b = o->b; po.p = o->G; po.batch = o->batch; po.dtype = o->dtype;
+    po.dims = o->dims;
     paco_status_t st = plan_build(out, &po, o->G, o->rank);
     if (st != PACO_OK || !o->restore) return st;
     if ((o->N1 * o->N2) / o->G > INT32_MAX) {

@@ -53,6 +53,7 @@ struct paco_plan {
     int form = 0;                  // tensor-core precision form (paco_tc.cuh), 0 = plain
     int req_ctas = 0;              // requested CTAs per SM of the stage kernels (0 = default)
     int req_split = 0;             // paco_plan_opts_t.split
+    int dims = 1;                  // 2: the 2-D DFT (the top-level twiddle tables hold ones)
     unsigned dbg_spin_limit = 0;   // paco_debug_set_waits: poll limit of the bounded waits (0 = default)
     unsigned dbg_wait_bias = 0;    // paco_debug_set_waits: added to the dependency targets
     void *tc = nullptr;            // its fragment table

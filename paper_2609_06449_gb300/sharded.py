@@ -42,10 +42,12 @@ def restore_maps(N1: int, N2: int, G: int, rank: int):
 
 class ShardedPlan:
     """``paco_plan_create_sharded``: the plan of rank ``rank`` of ``G``
-    (``restore``: also the maps of the second redistribution)."""
+    (``restore``: also the maps of the second redistribution; ``dims=2``:
+    the slab-decomposed 2-D DFT of the N1 x N2 view)."""
 
-    def __init__(self, N1: int, N2: int, b: int, G: int, rank: int, batch: int = 1, restore: bool = False):
-        o = ShardOpts(int(N1), int(N2), int(b), int(G), int(rank), int(batch), C64, 1 if restore else 0)
+    def __init__(self, N1: int, N2: int, b: int, G: int, rank: int, batch: int = 1, restore: bool = False,
+                 dims: int = 1):
+        o = ShardOpts(int(N1), int(N2), int(b), int(G), int(rank), int(batch), C64, 1 if restore else 0, int(dims))
         h = ctypes.c_void_p()
         _check(lib.paco_plan_create_sharded(ctypes.byref(h), ctypes.byref(o)))
         self._h = h

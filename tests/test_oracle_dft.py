@@ -124,3 +124,19 @@ def test_threaded_fft_is_bit_identical(lg, batch, d):
     one = oracle.fft(x, dir=d, threads=1)
     for t in (2, 3, 8):
         assert np.array_equal(oracle.fft(x, dir=d, threads=t), one)
+
+
+def test_oracle_2d_dft_against_numpy_fft2():
+    """The 2-D reference of the dims = 2 tests (the oracle's 1-D DFT down the
+    columns, then along the rows, returned transposed) against numpy's fft2,
+    an independent library routine, both directions."""
+    import oracle2d
+    rng = np.random.default_rng(17)
+    for N1, N2 in ((8, 16), (32, 32), (64, 8)):
+        x = rng.standard_normal((3, N1 * N2)) + 1j * rng.standard_normal((3, N1 * N2))
+        got = oracle2d.fft2_transposed(x, N1, N2, -1)
+        want = np.stack([np.fft.fft2(xi.reshape(N1, N2)).T.reshape(-1) for xi in x])
+        assert np.allclose(got, want, atol=1e-10 * np.abs(want).max())
+        got = oracle2d.fft2_transposed(x, N1, N2, +1)
+        want = np.stack([(N1 * N2 * np.fft.ifft2(xi.reshape(N1, N2))).T.reshape(-1) for xi in x])
+        assert np.allclose(got, want, atol=1e-10 * np.abs(want).max())
