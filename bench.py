@@ -18,19 +18,21 @@ paco_execute_host with pinned host buffers, the CPU oracle on a bounded
 sample, SM clocks sampled during the timed region, and cuFFT on the same
 input as context.
 
-Other workloads (--workload): A (2^16 as 256 x 256, latency), B128
-(complex128 N = 2^27), C (the uneven batch in one persistent launch), D
-(16 x 2^24 per precision form), E (forward + backward of 256 x 2^20 through
-the autograd function), U (the unfused three-pass pipeline Phase I ->
+Other workloads (--workload): A (2^16 as 256 x 256, latency: one cluster
+launch), B128 (complex128 N = 2^27), C (the uneven batch in one persistent
+launch), D (16 x 2^24 per precision form), E (forward + backward of
+256 x 2^20 with the weighted power loss fused into the stage kernels), T
+(the 128-point sub-pass of a 2^14 stage on the tcgen05 tensor cores against
+the plain FP32 kernel), U (the unfused three-pass pipeline Phase I ->
 paco_permute -> Phase III on the headline transform: the ablation of the
 fused redistribution).  Each prints one line of the same contract.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paco|reference]
-                  [--workload B|A|B128|C|D|E|U] [--dir -1|1]
+                  [--workload B|A|B128|C|D|E|T|U] [--dir -1|1]
 
 Under torchrun each rank runs an independent replica on its own GPU (the
-transform does not shard across GPUs on this path); timing is the max over
-ranks and `value` is the total over ranks.
+sharded form's exchange is not timed on this pool's one-GPU machines); timing
+is the max over ranks and `value` is the total over ranks.
 """
 
 from __future__ import annotations
