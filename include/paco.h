@@ -99,7 +99,20 @@ typedef struct {
                             sum_{j1,j2} x[j1 N2 + j2] w_N1^{-k1 j1} w_N2^{-k2 j2},
                             i.e. returned transposed (N2 x N1 row-major) -- the
                             same pipeline without the top-level twiddle: a slab
-                            decomposition of the 2-D FFT with one redistribution */
+                            decomposition of the 2-D FFT with one redistribution;
+                            3: the 3-D DFT of the N1 x N2 x N3 array (row-major,
+                            x[(j1 N2 + j2) N3 + j3]), returned with its axes
+                            reversed: out[(k3 N2 + k2) N1 + k1] = sum x[..]
+                            w_N1^{-k1 j1} w_N2^{-k2 j2} w_N3^{-k3 j3}.  The
+                            pipeline runs on the N1 x (N2 N3) view without the
+                            top-level twiddle, Phase III as two passes over the
+                            N2 x N3 planes (Sect. 4.1's top split, with ones for
+                            its twiddle).  complex64, not sharded; N2 and N3
+                            powers of b in 2^5..2^8 with N2 N3 <= 2^14; p must
+                            divide N1 and N2 N3; the weighted entry points
+                            reject it (PACO_ERR_UNSUPPORTED) */
+    int64_t N3;          /* dims = 3: the third axis; 0 (or 1) otherwise, else
+                            PACO_ERR_INVALID_ARG */
 } paco_plan_opts_t;
 
 /* Read-only description of a plan (paco_plan_info). */
@@ -121,7 +134,11 @@ typedef struct {
     int shard_rank;              /* sharded plan: this rank */
     int stage_split[2];          /* 1: the stage runs as two passes through the plan's
                                     N * batch scratch (complex64 stages of 2^12, 2^13) */
-    int dims;                    /* 1: the 1-D DFT; 2: the 2-D DFT of the N1 x N2 view */
+    int dims;                    /* 1: the 1-D DFT; 2: the 2-D DFT of the N1 x N2 view;
+                                    3: the 3-D DFT of the N1 x N2 x N3 array (m2, p,
+                                    items_per_pair, h and mu then refer to the
+                                    pipeline's second factor N2 N3) */
+    int64_t N3;                  /* dims = 3: the third axis; 1 otherwise */
 } paco_plan_info_t;
 
 /*

@@ -34,6 +34,7 @@ __all__ = [
     "library_path",
     "fft",
     "fft2",
+    "fft3",
     "PacoFFT",
     "PacoWeightedPowerLoss",
     "weighted_power_loss",
@@ -72,7 +73,7 @@ class PlanOpts(ctypes.Structure):
         ("N1", ctypes.c_int64), ("N2", ctypes.c_int64), ("b", ctypes.c_int),
         ("p", ctypes.c_int), ("batch", ctypes.c_int64), ("dtype", ctypes.c_int),
         ("tile_w", ctypes.c_int), ("cluster", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
-        ("split", ctypes.c_int), ("dims", ctypes.c_int),
+        ("split", ctypes.c_int), ("dims", ctypes.c_int), ("N3", ctypes.c_int64),
     ]
 
 
@@ -90,6 +91,7 @@ class PlanInfo(ctypes.Structure):
         ("shard_rank", ctypes.c_int),
         ("stage_split", ctypes.c_int * 2),
         ("dims", ctypes.c_int),
+        ("N3", ctypes.c_int64),
     ]
 
 
@@ -240,16 +242,16 @@ class Plan:
 
     def __init__(self, N1: int, N2: int, b: int, batch: int = 1, dtype: int = C64,
                  p: int = 0, tile_w: int = 0, cluster: int = 0, ctas_per_sm: int = 0, split: int = 0,
-                 dims: int = 1):
+                 dims: int = 1, N3: int = 0):
         o = PlanOpts(int(N1), int(N2), int(b), int(p), int(batch), int(dtype),
-                     int(tile_w), int(cluster), int(ctas_per_sm), int(split), int(dims))
+                     int(tile_w), int(cluster), int(ctas_per_sm), int(split), int(dims), int(N3))
         h = ctypes.c_void_p()
         _check(lib.paco_plan_create_ex(ctypes.byref(h), ctypes.byref(o)))
         self._h = h
         inf = PlanInfo()
         _check(lib.paco_plan_info(self._h, ctypes.byref(inf)))
         self.info = inf
-        self.N1, self.N2, self.N = inf.N1, inf.N2, inf.N
+        self.N1, self.N2, self.N3, self.N = inf.N1, inf.N2, inf.N3, inf.N
         self.b, self.p, self.batch, self.dtype = inf.b, inf.p, inf.batch, inf.dtype
         self.m1, self.m2 = inf.m1, inf.m2
 
@@ -366,7 +368,7 @@ def _dtype_code(t) -> int:
 
 
 def get_plan(N1: int, N2: int, b: int, batch: int, dtype: int, p: int = 0,
-             device: int | None = None, stream: int | None = None, dims: int = 1) -> Plan:
+             device: int | None = None, stream: int | None = None, dims: int = 1, N3: int = 0) -> Plan:
     """The cached plan for this shape on ``device`` and ``stream``.
 
     A plan's executions must not overlap in time (the 2^14 complex64 panel
@@ -377,11 +379,11 @@ def get_plan(N1: int, N2: int, b: int, batch: int, dtype: int, p: int = 0,
     dev = torch.cuda.current_device() if device is None else device
     if stream is None:
         stream = int(torch.cuda.current_stream(dev).cuda_stream)
-    key = (N1, N2, b, batch, dtype, p, dev, int(stream), int(dims))
+    key = (N1, N2, b, batch, dtype, p, dev, int(stream), int(dims), int(N3))
     pl = _PLANS.get(key)
     if pl is None:
         with torch.cuda.device(dev):
-            pl = Plan(N1, N2, b, batch, dtype, p, dims=dims)
+            pl = Plan(N1, N2, b, batch, dtype, p, dims=dims, N3=N3)
         _PLANS[key] = pl
     return pl
 
@@ -415,6 +417,31 @@ def fft2(x, N1: int, N2: int, b: int, p: int = 0, dir: int = -1, out=None):
     stream = int(torch.cuda.current_stream(x.device).cuda_stream)
     with torch.cuda.device(dev):
         pl = get_plan(int(N1), int(N2), int(b), batch, _dtype_code(x), int(p), dev, stream, dims=2)
+        pl.execute(x, out, dir, stream)
+    return out
+
+
+def fft3(x, N1: int, N2: int, N3: int, b: int, p: int = 0, dir: int = -1, out=None):
+    """3-D DFT of every N1 x N2 x N3 array in ``x`` (last dimension
+    N1*N2*N3, row major), returned with its axes reversed:
+    out[..., (k3 * N2 + k2) * N1 + k1] = sum x[..., (j1 * N2 + j2) * N3 + j3]
+    w_N1^{dir k1 j1} w_N2^{dir k2 j2} w_N3^{dir k3 j3} (a plan with dims = 3:
+    the pipeline on the N1 x (N2 N3) view without its top-level twiddle,
+    Phase III split over the N2 x N3 planes)."""
+    import torch
+    if not x.is_cuda:
+        raise ValueError("PACO runs on the GPU: x must be a CUDA tensor")
+    N = int(N1) * int(N2) * int(N3)
+    if x.shape[-1] != N:
+        raise ValueError(f"last dimension {x.shape[-1]} != N1*N2*N3 = {N}")
+    x = x.contiguous()
+    batch = x.numel() // N
+    if out is None:
+        out = torch.empty_like(x)
+    dev = x.device.index
+    stream = int(torch.cuda.current_stream(x.device).cuda_stream)
+    with torch.cuda.device(dev):
+        pl = get_plan(int(N1), int(N2), int(b), batch, _dtype_code(x), int(p), dev, stream, dims=3, N3=int(N3))
         pl.execute(x, out, dir, stream)
     return out
 

@@ -150,14 +150,17 @@ static const bool kDefaultTwoCtas = true;
 // near the memory bound (measured on GB300, one 2^28-point pass: L = 64
 // 0.76 ms, L = 128 0.71 ms, against 1.8-2.4 ms for L = 4096 and 3.2 ms for
 // L = 8192 in one pass).
-static paco_status_t setup_split(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode)
+static paco_status_t setup_split(paco_plan *pl, StageCfg *sc, int lgL, int64_t C, int mode, int lgLa_req = 0)
 {
     // pass lengths: powers of b (so that pi_m2(j_a Lb + j_b) = pi(j_b) La + pi(j_a)),
-    // La the larger, both between 2^5 and 2^8
-    int lgLa = (lgL + 1) / 2;
-    while (lgLa % pl->t) ++lgLa;
+    // both between 2^5 and 2^8; La the larger unless given (the 3-D DFT's middle axis)
+    int lgLa = lgLa_req;
+    if (!lgLa) {
+        lgLa = (lgL + 1) / 2;
+        while (lgLa % pl->t) ++lgLa;
+    }
     const int lgLb = lgL - lgLa;
-    if (lgLb % pl->t || lgLb < 5 || lgLa > 8) return PACO_OK;
+    if (lgLa % pl->t || lgLb % pl->t || lgLa < 5 || lgLb < 5 || lgLa > 8 || lgLb > 8) return PACO_OK;
     const int lgC = ilog2_exact(C);
     for (int p = 0; p < 2; ++p) {
         const int lgLs = p == 0 ? lgLa : lgLb;
@@ -195,7 +198,7 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
 {
     sc->lgL = lgL;
     if (!pl->form && !pl->shard_G && pl->esize == 8 && lgL == 14 && (mode == 1 || mode == 2) &&
-        C >= kPanelWidth && req_w == 0 && req_k == 0 && pl->req_split != 1) {
+        C >= kPanelWidth && req_w == 0 && req_k == 0 && pl->req_split != 1 && !(pl->dims == 3 && mode == 2)) {
         sc->panel = 1;
         sc->P = kPanelWidth;
         sc->fn = panel_kernel_fn(mode, pl->b);
@@ -256,7 +259,14 @@ static paco_status_t setup_stage(paco_plan *pl, StageCfg *sc, int lgL, int64_t C
         PACO_CUDA_TRY(cudaFuncSetAttribute(sc->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
         return PACO_OK;
     }
-    if (!pl->form && !pl->shard_G && pl->esize == 8 && pl->req_split >= 0 &&
+    if (pl->dims == 3 && mode == 2) {
+        // the 3-D DFT: Phase III is the N2' x N3 plane's two passes (whatever its length)
+        paco_status_t st = setup_split(pl, sc, lgL, C, mode, pl->lgLa3);
+        if (st != PACO_OK) return st;
+        if (!sc->split)
+            return fail(PACO_ERR_UNSUPPORTED, "dims = 3: no pass configuration for the %lld x %lld plane over %lld columns",
+                        1LL << pl->lgLa3, (long long)pl->N3, (long long)C);
+    } else if (!pl->form && !pl->shard_G && pl->esize == 8 && pl->req_split >= 0 &&
         (lgL == 12 || lgL == 13 || (lgL == 14 && pl->req_split == 1)) && mode != 3 && req_w == 0 && req_k == 0) {
         paco_status_t st = setup_split(pl, sc, lgL, C, mode);
         if (st != PACO_OK) return st;
@@ -276,6 +286,27 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
 {
     *out = nullptr;
     if (!o) return fail(PACO_ERR_INVALID_ARG, "opts is NULL");
+    // dims = 3: the N1 x N2' x N3 array is the pipeline's N1 x (N2' N3) view;
+    // Phase III runs as the split stage La x Lb = N2' x N3 with ones for its
+    // middle twiddle, i.e. the 2-D DFT of each N2' x N3 plane
+    paco_plan_opts_t o3;
+    int lgLa3 = 0;
+    if (o->dims == 3) {
+        if (shard_G) return fail(PACO_ERR_UNSUPPORTED, "dims = 3: not built for the sharded form");
+        if (o->dtype != PACO_C64) return fail(PACO_ERR_UNSUPPORTED, "dims = 3: complex64 only");
+        const int la = ilog2_exact(o->N2), lb = ilog2_exact(o->N3);
+        const int tb = (o->b == 2 || o->b == 4 || o->b == 8 || o->b == 16) ? ilog2_exact(o->b) : 1;
+        if (la < 5 || la > 8 || lb < 5 || lb > 8 || la % tb || lb % tb)
+            return fail(PACO_ERR_UNSUPPORTED, "dims = 3: N2=%lld and N3=%lld must be powers of b in 2^5..2^8",
+                        (long long)o->N2, (long long)o->N3);
+        if (la + lb > 14) return fail(PACO_ERR_UNSUPPORTED, "dims = 3: N2 N3 = 2^%d exceeds 2^14", la + lb);
+        o3 = *o;
+        o3.N2 = o->N2 * o->N3;
+        o = &o3;
+        lgLa3 = la;
+    } else if (o->N3 != 0 && o->N3 != 1) {
+        return fail(PACO_ERR_INVALID_ARG, "N3=%lld is for dims = 3 only", (long long)o->N3);
+    }
     if (o->b != 2 && o->b != 4 && o->b != 8 && o->b != 16)
         return fail(PACO_ERR_INVALID_ARG, "radix b=%d must be 2, 4, 8 or 16", o->b);
     if (o->dtype != PACO_C64 && o->dtype != PACO_C128 && o->dtype != PACO_C64_TC_BF16X3 &&
@@ -313,11 +344,13 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
     pl->shard_G = shard_G;
     pl->shard_rank = shard_rank;
     pl->req_split = o->split;
-    if (o->dims != 0 && o->dims != 1 && o->dims != 2) {
+    if (o->dims < 0 || o->dims > 3) {
         delete pl;
-        return fail(PACO_ERR_INVALID_ARG, "dims=%d must be 1 or 2", o->dims);
+        return fail(PACO_ERR_INVALID_ARG, "dims=%d must be 1, 2 or 3", o->dims);
     }
-    pl->dims = (o->dims == 2) ? 2 : 1;
+    pl->dims = (o->dims == 0) ? 1 : o->dims;
+    pl->lgLa3 = lgLa3;
+    pl->N3 = (o->dims == 3) ? o->N2 >> lgLa3 : 1;
     pl->req_ctas = o->ctas_per_sm;
     pl->form = (o->dtype == PACO_C64_TC_BF16X3) ? TC_BF16X3 : (o->dtype == PACO_C64_TC_FP16) ? TC_FP16 : TC_NONE;
     if (pl->form) {
@@ -344,11 +377,12 @@ static paco_status_t plan_build(paco_plan **out, const paco_plan_opts_t *o, int 
     const int lgN = l1 + l2;
     pl->twN_lo_bits = (lgN + 1) / 2;
     const long long nlo = 1LL << pl->twN_lo_bits, nhi = (1LL << lgN) / nlo;
-    const long long Mtw = (pl->dims == 2) ? 1 : pl->N;
+    const long long Mtw = (pl->dims >= 2) ? 1 : pl->N;
     if ((st = gen_table(pl->esize, &pl->twL1, pl->N1, pl->N1, 1, 0)) != PACO_OK ||
         (st = gen_table(pl->esize, &pl->twL2, pl->N2, pl->N2, 1, 0)) != PACO_OK ||
         (st = gen_table(pl->esize, &pl->twN_lo, Mtw, nlo, 1, 0)) != PACO_OK ||
-        (st = gen_table(pl->esize, &pl->twN_hi, Mtw, nhi, nlo, 0)) != PACO_OK) {
+        (st = gen_table(pl->esize, &pl->twN_hi, Mtw, nhi, nlo, 0)) != PACO_OK ||
+        (pl->dims == 3 && (st = gen_table(pl->esize, &pl->tw_ones, 1, pl->N2, 1, 0)) != PACO_OK)) {
         paco_plan_destroy(pl);
         return st;
     }
@@ -423,6 +457,7 @@ extern "C" void paco_plan_destroy(paco_plan_t *pl)
     cudaFree(pl->twN_lo);
     cudaFree(pl->twN_hi);
     cudaFree(pl->twN_full);
+    cudaFree(pl->tw_ones);
     cudaFree(pl->split_scratch);
     for (int k = 0; k < 2; ++k)
         for (int p = 0; p < 2; ++p) cudaFree(pl->st[k].sp_tw[p]);
@@ -440,7 +475,7 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
         batched_info(pl, info);
         return PACO_OK;
     }
-    info->N1 = pl->N1; info->N2 = pl->N2; info->N = pl->N; info->batch = pl->batch;
+    info->N1 = pl->N1; info->N2 = pl->N2 / pl->N3; info->N3 = pl->N3; info->N = pl->N; info->batch = pl->batch;
     info->b = pl->b; info->p = pl->p; info->m1 = pl->m1; info->m2 = pl->m2;
     info->dtype = pl->dtype;
     const int64_t line = 128 / pl->esize;
@@ -536,7 +571,7 @@ static paco_status_t launch_split(const paco_plan *pl, const StageCfg &sc, int m
         sa.lgLa = sc.lgLa;
         sa.lgLb = sc.lgLb;
         sa.rev_bits_c = (mode == 1) ? lgC : 0;
-        sa.twS = (mode == 1) ? pl->twL1 : pl->twL2;
+        sa.twS = (mode == 1) ? pl->twL1 : (pl->dims == 3) ? pl->tw_ones : pl->twL2;
         const void *src = (p == 0) ? in : pl->split_scratch;
         void *dst = (p == 0) ? pl->split_scratch : out;
         for (int64_t b0 = 0; b0 < pl->batch; b0 += 65535) {
@@ -785,6 +820,7 @@ extern "C" paco_status_t paco_shard_stage2(paco_plan_t *pl, const void *recv, vo
 static paco_status_t check_weighted(const paco_plan *pl, const char *fn)
 {
     if (pl->bs) return fail(PACO_ERR_UNSUPPORTED, "%s takes a single-length plan", fn);
+    if (pl->dims == 3) return fail(PACO_ERR_UNSUPPORTED, "%s: not built for dims = 3 plans", fn);
     if (pl->st[0].panel || pl->st[1].panel)
         return fail(PACO_ERR_UNSUPPORTED, "%s: plans with a 2^14 complex64 factor (panel stages) are not supported", fn);
     if (!pl->st[0].fn_terms || !pl->st[1].fn_terms)

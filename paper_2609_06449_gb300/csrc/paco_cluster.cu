@@ -355,7 +355,7 @@ paco_status_t cluster_setup(paco_plan *pl)
     PACO_CUDA_TRY(cudaFuncSetAttribute(cluster_kernel_fn(16), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        2 * 4096 * (int)sizeof(float2)));
     cluster_size();
-    return gen_table(8, &pl->twN_full, (pl->dims == 2) ? 1 : pl->N, pl->N, 1, 0);   // ones for the 2-D DFT
+    return gen_table(8, &pl->twN_full, (pl->dims >= 2) ? 1 : pl->N, pl->N, 1, 0);   // ones for the 2-D DFT
 }
 
 } // namespace paco

@@ -54,6 +54,9 @@ struct paco_plan {
     int req_ctas = 0;              // requested CTAs per SM of the stage kernels (0 = default)
     int req_split = 0;             // paco_plan_opts_t.split
     int dims = 1;                  // 2: the 2-D DFT (the top-level twiddle tables hold ones)
+    int64_t N3 = 1;                // dims = 3: the third axis; N2 (the pipeline's factor) is N2' N3
+    int lgLa3 = 0;                 // dims = 3: log2 of the middle axis N2' (Phase III's first split pass)
+    void *tw_ones = nullptr;       // dims = 3: ones in place of Phase III's split twiddle w_N2^{-k_a j_b}
     unsigned dbg_spin_limit = 0;   // paco_debug_set_waits: poll limit of the bounded waits (0 = default)
     unsigned dbg_wait_bias = 0;    // paco_debug_set_waits: added to the dependency targets
     void *tc = nullptr;            // its fragment table

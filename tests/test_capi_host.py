@@ -106,3 +106,33 @@ def test_tc_forms_reject_small_factors(dtype_name):
     with pytest.raises(paco.PacoError) as ei:
         paco.Plan(128, 256, 2, 1, getattr(paco, dtype_name))
     assert ei.value.status == 2 and "2^8" in str(ei.value)
+
+
+@pytest.mark.parametrize("N1,N2,N3,b,dtype_name,msg", [
+    (256, 16, 64, 2, "C64", "2^5..2^8"),        # N2 below one pass
+    (256, 64, 512, 2, "C64", "2^5..2^8"),       # N3 above one pass
+    (256, 128, 256, 2, "C64", "exceeds 2^14"),  # N2 N3 = 2^15
+    (256, 32, 64, 4, "C64", "powers of b"),     # 32 is not a power of 4
+    (256, 64, 48, 2, "C64", "powers of b"),
+    (256, 64, 64, 2, "C128", "complex64"),
+    (256, 64, 64, 2, "C64_TC_BF16X3", "complex64"),
+])
+def test_3d_plan_rejects_unsupported_shapes(N1, N2, N3, b, dtype_name, msg):
+    """dims = 3 checks its shape before touching a device."""
+    import paper_2609_06449_gb300 as paco
+    with pytest.raises(paco.PacoError) as ei:
+        paco.Plan(N1, N2, b, 1, getattr(paco, dtype_name), dims=3, N3=N3)
+    assert ei.value.status == 2 and msg in str(ei.value)
+
+
+def test_dims_and_n3_arguments_checked():
+    import paper_2609_06449_gb300 as paco
+    with pytest.raises(paco.PacoError) as ei:
+        paco.Plan(256, 256, 2, 1, paco.C64, N3=64)          # N3 without dims = 3
+    assert ei.value.status == 1 and "dims = 3" in str(ei.value)
+    with pytest.raises(paco.PacoError) as ei:
+        paco.Plan(256, 256, 2, 1, paco.C64, dims=4)
+    assert ei.value.status == 1 and "dims" in str(ei.value)
+    with pytest.raises(paco.PacoError) as ei:                 # the pipeline's factor N2 N3 checked too
+        paco.Plan(2 ** 15, 64, 2, 1, paco.C64, dims=3, N3=64)
+    assert "2^14" in str(ei.value)

@@ -623,26 +623,24 @@ def test_tc05_operand_layout_matches_descriptors(R):
 
 # ---- the split stages: the four passes' address maps compose to the DFT ------
 
-@pytest.mark.parametrize("N1,N2,b", [(64, 32, 2), (64, 64, 4), (128, 64, 2), (256, 16, 4)])
-@pytest.mark.parametrize("conj", [False, True])
-def test_split_stage_address_maps(N1, N2, b, conj):
+def _split_pipeline_model(xin, N1, N2, b, lgLa3=0):
     """Both stages as their two passes with the kernels' formulas: Phase I
     pass A (x viewed [La][Lb C], twiddle w_L^{-k_a j_b}, S[j_b][c][k_a]),
     pass B (S rows j_b, w_N^{-k1 c}, W[pi_m2(c)][k_a + La k_b]), Phase III
     pass A (W row pi(j_a) of block pi(j_b), S[j_b][k_a][v]) and pass B
-    (y[k_a + La k_b][v]); every slot written once; the result the DFT."""
+    (y[k_a + La k_b][v]); every slot written once.  lgLa3 > 0: the 3-D
+    form -- Phase III's first pass length La = 2^lgLa3 as given, ones for
+    the top-level twiddle and for Phase III's split twiddle."""
     import oracle
     t = {2: 1, 4: 2, 8: 3, 16: 4}[b]
     N = N1 * N2
-    rng = np.random.default_rng(N1 + N2 + b)
-    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
-    xin = np.conj(x) if conj else x
 
-    def split(L):
+    def split(L, lgLa=0):
         lgL = L.bit_length() - 1
-        lgLa = (lgL + 1) // 2
-        while lgLa % t:
-            lgLa += 1
+        if not lgLa:
+            lgLa = (lgL + 1) // 2
+            while lgLa % t:
+                lgLa += 1
         return 1 << lgLa, L >> lgLa
 
     def rev(u, bits):
@@ -675,10 +673,11 @@ def test_split_stage_address_maps(N1, N2, b, conj):
             k1 = ka + La * kb
             idx = rev(c, lgN2) * L + k1
             assert np.isnan(W[idx])
-            W[idx] = B[kb] * np.exp(-2j * np.pi * ((k1 * c) % N) / N)
+            top = 1.0 if lgLa3 else np.exp(-2j * np.pi * ((k1 * c) % N) / N)
+            W[idx] = B[kb] * top
     # Phase III (L = N2 over C = N1 columns), W as [N2][N1]
     L, C = N2, N1
-    La, Lb = split(L)
+    La, Lb = split(L, lgLa3)
     lgC = C.bit_length() - 1
     lgLa, lgLb = La.bit_length() - 1, Lb.bit_length() - 1
     S = np.full(N, np.nan, complex)
@@ -690,7 +689,7 @@ def test_split_stage_address_maps(N1, N2, b, conj):
         for ka in range(La):
             idx = ((jb * La + ka) * C) + v
             assert np.isnan(S[idx])
-            S[idx] = A[ka] * twL(L, ka * jb)
+            S[idx] = A[ka] * (1.0 if lgLa3 else twL(L, ka * jb))
     y = np.full(N, np.nan, complex)
     for cc in range(La * C):                             # view column k_a C + v
         ka, v = cc >> lgC, cc & (C - 1)
@@ -700,7 +699,36 @@ def test_split_stage_address_maps(N1, N2, b, conj):
             idx = (ka + La * kb) * N1 + v
             assert np.isnan(y[idx])
             y[idx] = B[kb]
+    return y
+
+
+@pytest.mark.parametrize("N1,N2,b", [(64, 32, 2), (64, 64, 4), (128, 64, 2), (256, 16, 4)])
+@pytest.mark.parametrize("conj", [False, True])
+def test_split_stage_address_maps(N1, N2, b, conj):
+    """The four passes of the split stages compose to the DFT."""
+    N = N1 * N2
+    rng = np.random.default_rng(N1 + N2 + b)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    y = _split_pipeline_model(np.conj(x) if conj else x, N1, N2, b)
     if conj:
         y = np.conj(y)
     want = np.fft.fft(x) if not conj else np.fft.ifft(x) * N
     assert np.allclose(y, want, atol=1e-9 * np.sqrt(N) * np.abs(want).max())
+
+
+@pytest.mark.parametrize("N1,Na,Nb,b", [(16, 8, 4, 2), (8, 4, 16, 2), (16, 16, 4, 4), (32, 4, 4, 4)])
+def test_split_stage_address_maps_3d(N1, Na, Nb, b):
+    """The same four passes with the 3-D plan's settings (ones for the
+    top-level twiddle and for Phase III's split twiddle, Phase III's first
+    pass length the middle axis Na, smaller or larger than Nb) compose to
+    the 3-D DFT of the N1 x Na x Nb array with its axes reversed; with the
+    default split or with the twiddles left in they do not."""
+    N2 = Na * Nb
+    N = N1 * N2
+    rng = np.random.default_rng(N1 + 3 * Na + 7 * Nb + b)
+    x = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    y = _split_pipeline_model(x, N1, N2, b, lgLa3=Na.bit_length() - 1)
+    want = np.fft.fftn(x.reshape(N1, Na, Nb)).transpose(2, 1, 0).reshape(-1)
+    assert np.allclose(y, want, atol=1e-9 * np.sqrt(N) * np.abs(want).max())
+    y1 = _split_pipeline_model(x, N1, N2, b)                 # the 1-D DFT instead
+    assert not np.allclose(y1, want, atol=1e-3 * np.abs(want).max())

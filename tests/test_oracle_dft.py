@@ -140,3 +140,21 @@ def test_oracle_2d_dft_against_numpy_fft2():
         got = oracle2d.fft2_transposed(x, N1, N2, +1)
         want = np.stack([(N1 * N2 * np.fft.ifft2(xi.reshape(N1, N2))).T.reshape(-1) for xi in x])
         assert np.allclose(got, want, atol=1e-10 * np.abs(want).max())
+
+
+def test_oracle_3d_dft_against_numpy_fftn():
+    """The 3-D reference of the dims = 3 tests (the oracle's 1-D DFT along
+    each axis in turn, returned with the axes reversed) against numpy's fftn,
+    an independent library routine, both directions; unequal axes, so that a
+    swapped pair of axes or a missed transpose fails."""
+    import oracle2d
+    rng = np.random.default_rng(23)
+    for N1, N2, N3 in ((4, 8, 16), (16, 4, 8), (8, 32, 2)):
+        N = N1 * N2 * N3
+        x = rng.standard_normal((2, N)) + 1j * rng.standard_normal((2, N))
+        got = oracle2d.fft3_reversed(x, N1, N2, N3, -1)
+        want = np.stack([np.fft.fftn(xi.reshape(N1, N2, N3)).transpose(2, 1, 0).reshape(-1) for xi in x])
+        assert np.allclose(got, want, atol=1e-10 * np.abs(want).max())
+        got = oracle2d.fft3_reversed(x, N1, N2, N3, +1)
+        want = np.stack([(N * np.fft.ifftn(xi.reshape(N1, N2, N3))).transpose(2, 1, 0).reshape(-1) for xi in x])
+        assert np.allclose(got, want, atol=1e-10 * np.abs(want).max())
