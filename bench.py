@@ -25,10 +25,12 @@ launch), D (16 x 2^24 per precision form), E (forward + backward of
 (the 128-point sub-pass of a 2^14 stage on the tcgen05 tensor cores against
 the plain FP32 kernel), U (the unfused three-pass pipeline Phase I ->
 paco_permute -> Phase III on the headline transform: the ablation of the
-fused redistribution).  Each prints one line of the same contract.
+fused redistribution), F3 (64 complex64 3-D DFTs of 256 x 64 x 64, the
+dims = 3 plan, with cuFFT's fftn as context).  Each prints one line of the
+same contract.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl paco|reference]
-                  [--workload B|A|B128|C|D|E|T|U] [--dir -1|1]
+                  [--workload B|A|B128|C|D|E|T|U|F3] [--dir -1|1]
 
 Under torchrun each rank runs an independent replica on its own GPU (the
 sharded form's exchange is not timed on this pool's one-GPU machines); timing
@@ -71,7 +73,7 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["B", "A", "B128", "C", "D", "E", "U", "T"], default="B")
+    ap.add_argument("--workload", choices=["B", "A", "B128", "C", "D", "E", "U", "T", "F3"], default="B")
     ap.add_argument("--small", action="store_true",
                     help="a reduced case of the workload (C: 1024 lengths to 2^26 + 4096 x 2^12; D: batch 2; "
                          "U: N = 2^26; T: 2^24 points), for ncu captures")
@@ -758,6 +760,49 @@ def run_other(args, ranks, local):
                     hbm_gbs_effective=48.0 * N * world / (ms * 1e-3) / 1e9,
                     roofline=hbm_roofline("paco_permute_kernel", 16.0 * N, sp[1]),
                     e2e=None, cpu_baseline=cpu_leg(args, rank, world), gpu_launches=3 * K, clocks=clocks)
+    elif wl == "F3":
+        # the 3-D DFT (dims = 3) of 64 arrays of 256 x 64 x 64, with cuFFT's fftn on the same input as context
+        N1, N2, N3 = 256, 64, 64
+        N, B = N1 * N2 * N3, (8 if args.small else 64)
+        xh = torch.from_numpy(uniform(N * B, rank, np.complex64)).pin_memory()
+        x = xh.cuda()
+        y = torch.empty_like(x)
+        plan = paco.Plan(N1, N2, 2, B, paco.C64, dims=3, N3=N3)
+        launches = 2 + sum(plan.info.stage_split)
+        for _ in range(W):
+            plan.execute(x, y, -1, stream)
+        tot, per, clocks = timed(lambda: plan.execute(x, y, -1, stream))
+        plan.check()
+        ms = mor(tot) / K
+        flop = 5.0 * N * math.log2(N) * B
+        xv = x.view(B, N1, N2, N3)
+        ctot, cper = time_steps(lambda: torch.fft.fftn(xv, dim=(1, 2, 3)), min(K, 20), 3, stream)
+        ref = torch.fft.fftn(xv, dim=(1, 2, 3)).permute(0, 3, 2, 1).reshape(B * N)
+        torch.cuda.synchronize()
+        diff = float(torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref))
+        cms = statistics.median(cper)
+        ho = torch.empty_like(xh).pin_memory()
+        di = torch.empty_like(x)
+        line = dict(base, value=flop * world / (ms * 1e-3) / 1e9, unit="GFLOP/s", higher_is_better=True,
+                    ms_per_step=ms, dtype="f32",
+                    config={"workload": f"{B} x c64 3-D DFT of {N1} x {N2} x {N3} (dims = 3, b = 2), forward, "
+                                        "output axes reversed",
+                            "N1": N1, "N2": N2, "N3": N3, "batch": B, "input": "Re, Im i.i.d. U[-1,1), seed = rank",
+                            "l2": "inputs larger than L2"},
+                    stage_split=list(plan.info.stage_split), launches_per_step=launches,
+                    hbm_gbs_effective=16.0 * launches * N * B * world / (ms * 1e-3) / 1e9,
+                    accuracy={"rel_l2_vs_cufft_fftn": diff,
+                              "measured_on": "the whole output vs torch.fft.fftn (parity with the oracle is in the tests)"},
+                    context={"cufft_fftn_ms_per_step": cms, "cufft_gflops": flop / (cms * 1e-3) / 1e9,
+                             "source": "torch.fft.fftn over the three axes (cuFFT), same input, median of %d"
+                                       % min(K, 20)},
+                    roofline=hbm_roofline(f"stage kernels, {launches} passes (Phase III split over the "
+                                          f"{N2} x {N3} planes)", 16.0 * N * B, statistics.mean(per) / launches),
+                    e2e=None if args.no_e2e else e2e_host(lambda: plan.execute_host(xh, ho, di, y, -1, stream),
+                                                          max(args.e2e_steps, 1), stream, flop / 1e9, "GFLOP/s",
+                                                          N * B * 8, N * B * 8, "paco_execute_host (pinned host buffers)",
+                                                          mor, world, ranks.barrier),
+                    cpu_baseline=None, gpu_launches=K * launches, clocks=clocks)
     else:  # E
         N1 = N2 = 1024
         N, B = N1 * N2, 256
