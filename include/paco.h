@@ -233,7 +233,8 @@ typedef struct {
     paco_dtype_t dtype;  /* PACO_C64 */
     int restore;         /* 1: also build the maps of paco_shard_restore_* */
     int dims;            /* 2: the 2-D DFT of the N1 x N2 view (as paco_plan_opts_t.dims):
-                            the slab-decomposed 2-D FFT across the G ranks */
+                            the slab-decomposed 2-D FFT across the G ranks; 3 is
+                            not built for the sharded form (PACO_ERR_UNSUPPORTED) */
 } paco_shard_opts_t;
 
 paco_status_t paco_plan_create_sharded(paco_plan_t **out, const paco_shard_opts_t *opts);

@@ -471,6 +471,7 @@ extern "C" paco_status_t paco_plan_info(const paco_plan_t *pl, paco_plan_info_t 
 {
     if (!pl || !info) return fail(PACO_ERR_INVALID_ARG, "NULL argument");
     memset(info, 0, sizeof(*info));
+    info->N3 = 1;
     if (pl->bs) {
         batched_info(pl, info);
         return PACO_OK;

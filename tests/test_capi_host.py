@@ -136,3 +136,12 @@ def test_dims_and_n3_arguments_checked():
     with pytest.raises(paco.PacoError) as ei:                 # the pipeline's factor N2 N3 checked too
         paco.Plan(2 ** 15, 64, 2, 1, paco.C64, dims=3, N3=64)
     assert "2^14" in str(ei.value)
+
+
+def test_sharded_plan_rejects_dims_3():
+    """The 3-D form is not built for the sharded form: refused before any device work."""
+    import paper_2609_06449_gb300 as paco
+    from paper_2609_06449_gb300.sharded import ShardedPlan
+    with pytest.raises(paco.PacoError) as ei:
+        ShardedPlan(256, 1024, 2, 4, 0, dims=3)
+    assert ei.value.status == 2 and "sharded" in str(ei.value)
