@@ -31,6 +31,7 @@
 // whatever landed.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstring>
 
 #include "../../include/paco.h"
@@ -274,12 +275,17 @@ bool cluster_eligible(const paco_plan *pl)
            pl->batch <= 16;
 }
 
-// CTAs per transform: 16 when a 16-CTA cluster of this kernel can be resident, else 8.
+// CTAs per transform on the current device: 16 when a 16-CTA cluster of this
+// kernel can be resident, else 8 (queried once per device; concurrent first
+// calls compute the same answer).
 int cluster_size()
 {
-    static int k = 0;
-    if (k) return k;
-    k = 8;
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    const int known = cache[dev].load(std::memory_order_relaxed);
+    if (known) return known;
+    int k = 8;
     if (cudaFuncSetAttribute(cluster_kernel_fn(16), cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
         cudaSuccess) {
         cudaLaunchConfig_t cfg;
@@ -298,6 +304,7 @@ int cluster_size()
         if (cudaOccupancyMaxActiveClusters(&n, cluster_kernel_fn(16), &cfg) == cudaSuccess && n > 0) k = 16;
     }
     cudaGetLastError();                                       // a refused query leaves no error behind
+    cache[dev].store(k, std::memory_order_relaxed);
     return k;
 }
 
@@ -318,7 +325,7 @@ paco_status_t launch_cluster(const paco_plan *pl, const void *in, void *out, int
     a.pair_count = pair_count;
     a.wait_ns = 2000000000ull;
     a.extra_tx = 8u * pl->dbg_wait_bias;          // paco_debug_set_waits: a wait that runs out
-    const int K = cluster_size();
+    const int K = pl->fused_k;                    // chosen at plan creation on the plan's device
     const int threads = (int)(pl->N / K / 16);
     const size_t smem = 2 * (size_t)(pl->N / K) * sizeof(float2);
     for (int64_t b0 = 0; b0 < pl->batch; b0 += 8192) {
@@ -354,7 +361,7 @@ paco_status_t cluster_setup(paco_plan *pl)
                                        2 * 8192 * (int)sizeof(float2)));
     PACO_CUDA_TRY(cudaFuncSetAttribute(cluster_kernel_fn(16), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        2 * 4096 * (int)sizeof(float2)));
-    cluster_size();
+    pl->fused_k = cluster_size();
     return gen_table(8, &pl->twN_full, (pl->dims >= 2) ? 1 : pl->N, pl->N, 1, 0);   // ones for the 2-D DFT
 }
 

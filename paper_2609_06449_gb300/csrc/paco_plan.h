@@ -61,6 +61,7 @@ struct paco_plan {
     unsigned dbg_wait_bias = 0;    // paco_debug_set_waits: added to the dependency targets
     void *tc = nullptr;            // its fragment table
     int fused = 0;                 // 1: paco_execute is one cluster launch (paco_cluster.cu)
+    int fused_k = 8;               //   its CTAs per transform (16 where the device allows that cluster)
     void *twN_full = nullptr;      // one-launch form: w_N^{-r}, r < N
     void *split_scratch = nullptr; // split stages: the intermediate of their two passes (N * batch)
     int shard_G = 0;               // sharded form (paco_plan_create_sharded): ranks, 0 = not sharded
