@@ -7,10 +7,12 @@ been built (``python -c "import __graft_entry__ as g; g.build()"``).
 
 Entry points (same names as the C ABI):
 
-* ``Plan(N1, N2, b, batch, dtype, p=0, tile_w=0, cluster=0)`` --
-  ``paco_plan_create_ex``; ``.execute(in_ptr, out_ptr, dir, stream)`` etc.
+* ``Plan(N1, N2, b, batch, dtype, p=0, tile_w=0, cluster=0, ctas_per_sm=0,
+  split=0, dims=1, N3=0)`` -- ``paco_plan_create_ex``;
+  ``.execute(in_ptr, out_ptr, dir, stream)`` etc.
 * ``fft(x, N1, N2, b, p=0, dir=-1)`` -- torch tensors on the GPU;
-  ``fft2`` -- the 2-D DFT of the N1 x N2 view (transposed result).
+  ``fft2`` -- the 2-D DFT of the N1 x N2 view (transposed result);
+  ``fft3`` -- the 3-D DFT of N1 x N2 x N3 arrays (axes reversed).
 * ``PacoFFT`` -- ``torch.autograd.Function`` whose backward is the conjugate
   transform (``dir=+1``).
 * ``sharded`` -- the sharded form across G ranks (``ShardedPlan``,
@@ -238,7 +240,9 @@ def _stream(stream) -> int:
 class Plan:
     """A PACO plan (``paco_plan_create_ex``).  Buffers are torch tensors or
     raw device pointers; ``stream`` is a torch stream, a raw handle, or None
-    for torch's current stream."""
+    for torch's current stream.  ``dims=2``: the 2-D DFT of the N1 x N2 view;
+    ``dims=3`` with ``N3``: the 3-D DFT of N1 x N2 x N3 arrays (then
+    ``self.N2`` is the middle axis and ``self.N`` = N1 N2 N3)."""
 
     def __init__(self, N1: int, N2: int, b: int, batch: int = 1, dtype: int = C64,
                  p: int = 0, tile_w: int = 0, cluster: int = 0, ctas_per_sm: int = 0, split: int = 0,
