@@ -19,6 +19,7 @@
 #include "../../include/paco.h"
 #include "paco_plan.h"
 #include "paco_common.cuh"
+#include "paco_stage_args.cuh"
 #include "paco_panel_host.h"
 #include "paco_stage.cuh"
 

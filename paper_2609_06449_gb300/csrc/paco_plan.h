@@ -23,7 +23,7 @@ struct StageCfg {
     int panel = 0;    // 1: L2-resident panel pipeline (paco_panel.cuh)
     int P = 0;        // panel width (columns)
     // split = 1: the stage runs as two passes through the plan's scratch (pass A
-    // of length 2^lgLa, pass B of length 2^lgLb; SplitArgs in paco_common.cuh)
+    // of length 2^lgLa, pass B of length 2^lgLb; SplitArgs in paco_stage_args.cuh)
     int split = 0;
     int lgLa = 0, lgLb = 0;
     int sp_lgW[2] = {0, 0}, sp_threads[2] = {0, 0}, sp_smem[2] = {0, 0}, sp_ntiles[2] = {0, 0};

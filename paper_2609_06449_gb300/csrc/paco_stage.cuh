@@ -39,6 +39,7 @@
 #include <cooperative_groups.h>
 
 #include "paco_common.cuh"
+#include "paco_stage_args.cuh"
 #include "paco_tc.cuh"
 
 namespace paco {
